@@ -1,0 +1,321 @@
+"""FP64 CPU oracle of the calibration hot path (test infrastructure only).
+
+The paper (Spreeuw et al., "GPU acceleration of the SAGECal calibration
+package for the SKA") times SAGECal's CPU and GPU builds calibrating clustered
+sky models (§2: "a single calibration solution will be derived for each
+cluster") on arrays whose data size grows as the N(N-1)/2 baselines (§3).  It
+prints no equation; the method it times is SAGECal's:
+
+* the radio-interferometric measurement equation (Hamaker, Bregman & Sault
+  1996): per cluster k, V_pq = J_kp C_kpq J_kq^H with 2x2 complex Jones
+  matrices J and the point-source coherency
+  C_pq(t, f) = sum_s S_s(f) exp(-2 pi i f/c (u l_s + v m_s + w (n_s - 1))) Id;
+* Levenberg-Marquardt on the Gauss-Newton normal equations J^T J, J^T r
+  (Madsen, Nielsen & Tingleff 2004, Alg. 3.16, Marquardt's diagonal scaling),
+  each damped system solved by a Cholesky factorisation;
+* SAGE/EM (Fessler & Hero 1994; Kazemi et al. 2011, SAGECal's solver): the
+  clusters are solved one at a time, cluster k against the data minus the
+  current models of all other clusters.
+
+Everything is float64 / complex128.  Plain and slow by design: the Jacobian is
+built row by row from its definition (product rule on J_p C J_q^H), J^T J is
+summed from those rows, and the LM loop follows the textbook order.  Library
+steps: numpy.linalg.cholesky and scipy's triangular solves; numpy.linalg.svd
+for the Procrustes alignment.
+
+Conventions
+-----------
+* baselines b = (p, q), p < q, ordered b = p*N - p(p+1)/2 + (q-p-1)
+* station (u, v, w) in metres, [T][N][3]; baseline uvw_pq = uvw_p - uvw_q
+* visibilities [T][B][F][2][2] complex, coherencies [T][B][F] complex (the
+  unpolarised brightness matrix is a multiple of the identity)
+* parameters of station s: theta[8s + 4i + 2j + 0/1] = Re/Im J_s[i, j]
+* "Jhr" = J^T r with r = X - model (so the LM step solves (A + mu D) d = Jhr)
+
+What pins each function (tests/test_oracle.py):
+* predict_coherencies: a unit source at the phase centre gives exactly 1;
+  a source given by (hour angle, declination) gives the phase of its
+  geometric delay (x_p - x_q).(s - s0) f/c computed in the equatorial frame;
+  Hermitian swap of p and q; linearity in sources; spectral law at l=m=0.
+* normal_equations: central finite differences of the residual on 4 stations;
+  gradient of the cost; gauge generators in the null space of J^T J.
+* cholesky_solve: reconstruction and exact integer systems.
+* levenberg_marquardt: a linear least-squares problem (rho = 1, mu/3 per
+  step, exact solution); Rosenbrock's function; noiseless recovery of the
+  true Jones up to the unitary ambiguity; the chi^2 statistic of the noisy
+  minimum; a multistart search on 3 stations finds no lower cost.
+* sage_calibrate: K = 1 is the single-cluster LM bit for bit; noiseless
+  multi-cluster recovery; the total cost never increases over EM sweeps.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg
+
+C_LIGHT = 299792458.0
+
+
+# --- layout -------------------------------------------------------------------
+
+def baselines(N: int):
+    """(p, q) of every baseline, p < q, in baseline-index order."""
+    p, q = [], []
+    for a in range(N):
+        for b in range(a + 1, N):
+            p.append(a)
+            q.append(b)
+    return np.array(p, dtype=np.int64), np.array(q, dtype=np.int64)
+
+
+def jones_to_theta(J: np.ndarray) -> np.ndarray:
+    """[N][2][2] complex -> [8N] real, theta[8s+4i+2j] = Re, +1 = Im."""
+    N = J.shape[0]
+    th = np.empty((N, 2, 2, 2))
+    th[..., 0] = J.real
+    th[..., 1] = J.imag
+    return th.reshape(8 * N)
+
+
+def theta_to_jones(theta: np.ndarray) -> np.ndarray:
+    th = theta.reshape(-1, 2, 2, 2)
+    return th[..., 0] + 1j * th[..., 1]
+
+
+# --- prediction ---------------------------------------------------------------
+
+def predict_coherencies(uvw, freqs, l, m, flux, alpha, f0=150e6):
+    """Point-source coherencies of one cluster, [T][B][F] complex128.
+
+    C_pq(t,f) = sum_s S_s(f) exp(-2 pi i (f/c)(u l_s + v m_s + w (n_s - 1)))
+    with S_s(f) = S_s (f/f0)^alpha_s, n_s = sqrt(1 - l_s^2 - m_s^2) and
+    (u, v, w) the baseline coordinates uvw_p - uvw_q at timeslot t.
+    """
+    uvw = np.asarray(uvw, dtype=np.float64)
+    T, N, _ = uvw.shape
+    p, q = baselines(N)
+    l = np.asarray(l, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    n = np.sqrt(1.0 - l * l - m * m)
+    F = len(freqs)
+    out = np.zeros((T, len(p), F), dtype=np.complex128)
+    for t in range(T):
+        b = uvw[t, p, :] - uvw[t, q, :]                       # [B][3]
+        path = (np.outer(b[:, 0], l) + np.outer(b[:, 1], m)
+                + np.outer(b[:, 2], n - 1.0))                 # [B][S] metres
+        for fi, f in enumerate(freqs):
+            S = np.asarray(flux) * (f / f0) ** np.asarray(alpha)
+            out[t, :, fi] = np.exp(-2j * np.pi * (f / C_LIGHT) * path) @ S
+    return out
+
+
+def predict_sky(uvw, freqs, sky):
+    """Coherencies of every cluster of a `synth.Sky`: [K][T][B][F]."""
+    return np.stack([
+        predict_coherencies(uvw, freqs, sky.l[a:b], sky.m[a:b], sky.flux[a:b],
+                            sky.alpha[a:b], sky.f0)
+        for a, b in zip(sky.offsets[:-1], sky.offsets[1:])])
+
+
+# --- measurement equation -----------------------------------------------------
+
+def model_vis(C, J):
+    """J_p (C_pq Id) J_q^H for every vis: [T][B][F][2][2]."""
+    N = J.shape[0]
+    p, q = baselines(N)
+    G = J[p] @ np.conj(np.swapaxes(J[q], -1, -2))             # [B][2][2]
+    return C[..., None, None] * G[None, :, None, :, :]
+
+
+def residual(X, C, J):
+    """R = X - J_p C J_q^H and cost = sum |R|^2 (squared Frobenius norms)."""
+    R = X - model_vis(C, J)
+    return R, float(np.sum(R.real ** 2 + R.imag ** 2))
+
+
+def simulate(uvw, freqs, sky, J_true, noise=None):
+    """V = sum_k model_k + noise, and the coherencies [K][T][B][F]."""
+    Cs = predict_sky(uvw, freqs, sky)
+    V = sum(model_vis(Cs[k], J_true[k]) for k in range(len(Cs)))
+    if noise is not None:
+        V = V + noise
+    return V, Cs
+
+
+# --- Jacobian and normal equations ---------------------------------------------
+
+def _unit(i, j, imag):
+    E = np.zeros((2, 2), dtype=np.complex128)
+    E[i, j] = 1j if imag else 1.0
+    return E
+
+
+def model_jacobian(C, J):
+    """Real Jacobian of the model per vis, [T][B][F][8][16].
+
+    Rows: Re of the 4 entries of M = C J_p J_q^H, then Im of the 4 entries.
+    Columns: the 8 parameters of J_p, then the 8 of J_q (theta order).  By
+    the product rule, dM = C (dJ_p J_q^H + J_p dJ_q^H), with dJ the unit
+    change of one real parameter.
+    """
+    N = J.shape[0]
+    p, q = baselines(N)
+    Jp, Jq = J[p], J[q]
+    JqH = np.conj(np.swapaxes(Jq, -1, -2))
+    cols = []
+    for side in (0, 1):
+        for i in range(2):
+            for j in range(2):
+                for imag in (0, 1):
+                    dJ = _unit(i, j, imag)
+                    if side == 0:
+                        d = dJ[None] @ JqH                     # dJ_p J_q^H
+                    else:
+                        d = Jp @ np.conj(dJ.T)[None]           # J_p dJ_q^H
+                    cols.append(d.reshape(-1, 4))              # [B][4]
+    D = np.stack(cols, axis=-1)                                # [B][4][16]
+    dM = C[..., None, None] * D[None, :, None, :, :]           # [T][B][F][4][16]
+    return np.concatenate([dM.real, dM.imag], axis=-2)         # [T][B][F][8][16]
+
+
+def normal_equations(R, C, J, t_chunk=4):
+    """Gauss-Newton normal equations A = J^T J ([8N][8N]) and g = J^T r ([8N])
+    of the cost sum |X - C J_p J_q^H|^2 at residual R = X - model."""
+    N = J.shape[0]
+    p, q = baselines(N)
+    T = C.shape[0]
+    P = 8 * N
+    blocks = np.zeros((len(p), 16, 16))
+    grads = np.zeros((len(p), 16))
+    for t0 in range(0, T, t_chunk):
+        Jv = model_jacobian(C[t0:t0 + t_chunk], J)             # [t][B][F][8][16]
+        Rt = R[t0:t0 + t_chunk].reshape(*R[t0:t0 + t_chunk].shape[:3], 4)
+        r = np.concatenate([Rt.real, Rt.imag], axis=-1)        # [t][B][F][8]
+        blocks += np.einsum("tbfrk,tbfrl->bkl", Jv, Jv)
+        grads += np.einsum("tbfrk,tbfr->bk", Jv, r)
+    A = np.zeros((N, 8, N, 8))
+    g = np.zeros((N, 8))
+    for b in range(len(p)):
+        s = (p[b], q[b])
+        for x in range(2):
+            g[s[x]] += grads[b, 8 * x:8 * x + 8]
+            for y in range(2):
+                A[s[x], :, s[y], :] += blocks[b, 8 * x:8 * x + 8, 8 * y:8 * y + 8]
+    return A.reshape(P, P), g.reshape(P)
+
+
+# --- linear algebra -----------------------------------------------------------
+
+def cholesky_solve(A, b):
+    """Solve A x = b for symmetric positive definite A: A = L L^T, then
+    L y = b and L^T x = y.  Raises numpy.linalg.LinAlgError if A is not PD."""
+    L = np.linalg.cholesky(A)
+    y = scipy.linalg.solve_triangular(L, b, lower=True)
+    return scipy.linalg.solve_triangular(L.T, y, lower=False)
+
+
+# --- Levenberg-Marquardt ------------------------------------------------------
+
+def levenberg_marquardt(evaluate, theta0, n_iter, tau=1e-3, eps_grad=1e-12,
+                        trace=None):
+    """Levenberg-Marquardt with Marquardt scaling (Madsen, Nielsen & Tingleff
+    2004, Alg. 3.16 with D = diag(J^T J)).
+
+    evaluate(theta) -> (cost, A, g): cost = |r|^2, A = J^T J, g = J^T r with
+    r = data - model, so that the step d solves (A + mu diag(A)) d = g.
+
+    mu starts at tau * max diag(A), nu at 2.  Each of the n_iter iterations
+    tries one step; the gain ratio rho = (cost - cost_trial) / (d^T (mu D d
+    + g)) accepts it when rho > 0 (then mu *= max(1/3, 1 - (2 rho - 1)^3),
+    nu = 2), else mu *= nu, nu *= 2.  Iterations stop early once
+    max|g| <= eps_grad * (1 + cost).  A damped matrix that is not positive
+    definite counts as a rejected step.
+    Returns (theta, cost, iterations done).
+    """
+    theta = np.array(theta0, dtype=np.float64)
+    cost, A, g = evaluate(theta)
+    mu = tau * float(np.max(np.diag(A)))
+    nu = 2.0
+    done = 0
+    for _ in range(n_iter):
+        if float(np.max(np.abs(g))) <= eps_grad * (1.0 + cost):
+            break
+        done += 1
+        D = np.diag(A).copy()
+        try:
+            d = cholesky_solve(A + mu * np.diag(D), g)
+        except np.linalg.LinAlgError:
+            mu *= nu
+            nu *= 2.0
+            continue
+        trial = theta + d
+        cost_t, A_t, g_t = evaluate(trial)
+        pred = float(d @ (mu * D * d + g))
+        rho = (cost - cost_t) / pred if pred > 0.0 else -1.0
+        if trace is not None:
+            trace.append(dict(mu=mu, nu=nu, rho=rho, cost=cost, cost_trial=cost_t))
+        if rho > 0.0:
+            theta, cost, A, g = trial, cost_t, A_t, g_t
+            mu *= max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
+            nu = 2.0
+        else:
+            mu *= nu
+            nu *= 2.0
+    return theta, cost, done
+
+
+def lm_cluster(X, C, J0, n_lm, tau=1e-3, eps_grad=1e-12, trace=None):
+    """Solve one cluster: minimise sum |X - C J_p J_q^H|^2 over the Jones.
+    Returns (J, final cost, iterations done)."""
+    def evaluate(theta):
+        J = theta_to_jones(theta)
+        R, cost = residual(X, C, J)
+        A, g = normal_equations(R, C, J)
+        return cost, A, g
+    theta, cost, done = levenberg_marquardt(evaluate, jones_to_theta(J0), n_lm,
+                                            tau, eps_grad, trace)
+    return theta_to_jones(theta), cost, done
+
+
+# --- SAGE / EM ----------------------------------------------------------------
+
+def sage_calibrate(V, Cs, J0, n_em, n_lm, tau=1e-3, eps_grad=1e-12,
+                   sweep_costs=None):
+    """SAGE: for each EM iteration and each cluster k in ascending order, the
+    E-step forms the data of cluster k, X_k = V - sum_{j != k} model_j, from
+    the current solutions of the other clusters; the M-step solves cluster k
+    on X_k by LM, warm-started from its current Jones.
+    Returns (J [K][N][2][2], final LM cost of each cluster)."""
+    K = len(Cs)
+    J = np.array(J0, dtype=np.complex128)
+    costs = np.zeros(K)
+    for _ in range(n_em):
+        for k in range(K):
+            X = V.copy()
+            for j in range(K):
+                if j != k:
+                    X = X - model_vis(Cs[j], J[j])
+            J[k], costs[k], _ = lm_cluster(X, Cs[k], J[k], n_lm, tau, eps_grad)
+        if sweep_costs is not None:
+            R = V - sum(model_vis(Cs[j], J[j]) for j in range(K))
+            sweep_costs.append(float(np.sum(R.real ** 2 + R.imag ** 2)))
+    return J, costs
+
+
+# --- comparison up to the unitary ambiguity -----------------------------------
+
+def align_unitary(J, J_ref):
+    """Unitary U minimising sum_p |J_p U - J_ref,p|_F^2 (orthogonal
+    Procrustes): U = W Z^H from the SVD W S Z^H of sum_p J_p^H J_ref,p.
+    J_p -> J_p U leaves every J_p C J_q^H unchanged."""
+    M = np.einsum("pji,pjk->ik", np.conj(J), J_ref)
+    W, _, Zh = np.linalg.svd(M)
+    return W @ Zh
+
+
+def aligned_error(J, J_ref):
+    """max_p |J_p U - J_ref,p|_F / |J_ref,p|_F after Procrustes alignment."""
+    U = align_unitary(J, J_ref)
+    d = np.linalg.norm(J @ U - J_ref, axis=(1, 2))
+    return float(np.max(d / np.linalg.norm(J_ref, axis=(1, 2))))
