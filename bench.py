@@ -1,0 +1,456 @@
+#!/usr/bin/env python
+"""Throughput of SAGE/EM direction-dependent calibration on GB300.
+
+One step = one sc_calibrate_sage call on one job (predict every cluster,
+then n_em SAGE sweeps of n_lm Levenberg-Marquardt iterations per cluster)
+with the job's inputs resident in HBM.  The metric counts, per second,
+visibilities x clusters x LM iterations:
+
+    value = (B * T * F) * K * n_lm * n_em * steps * n_gpus / seconds
+
+Default workload: SKA1-LOW scale, 512 stations (130816 baselines), 10
+timeslots, 4 channels 140-160 MHz, 40 clusters x 100 sources, 5 SAGE sweeps x
+10 LM iterations, mixed precision (float32 data and factorisation, float64
+phase argument, Jones state and step refinement).  Inputs are synthetic,
+shaped like the paper's 512-station dataset (paper §2).
+
+With --gpus N (launched by torchrun) every rank calibrates its own job (an
+independent sub-band, seed = rank): no collective on the data path, weak
+scaling; the barrier and the max over ranks only frame the timing.
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1910_13908_gb300 import synth  # noqa: E402
+
+METRIC = "vis·cluster/s per LM iter"
+UNIT = "vis·cluster·iter/s"
+
+WORKLOADS = {
+    # name: (config, n_em, n_lm, description)
+    "ska512": ("c4", 5, 10, "SKA1-LOW scale: 512 stations (130816 baselines), 10 timeslots, "
+                            "4 channels 140-160 MHz, 40 clusters x 100 sources, 5 SAGE sweeps x 10 LM"),
+    "precision128": ("c2", 3, 10, "128 stations (8128 baselines), 20 timeslots, 8 channels 140-160 MHz "
+                                  "(spectral index -0.7), 10 clusters x 25 sources, 3 SAGE sweeps x 10 LM"),
+    "lofar64": ("c1", 1, 10, "64 stations (2016 baselines), 10 timeslots, 1 channel at 150 MHz, "
+                             "1 cluster x 20 sources, 10 LM"),
+}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --- the FP64 CPU oracle on a bounded sample (cpu_baseline and --impl reference) -------------
+
+def oracle_sample(n_lm=1, N=512, S=100, seed=0):
+    """Times the oracle (as it stands) on a bounded sample of the workload:
+    N stations, 1 timeslot, 1 channel, one cluster of S sources: prediction
+    plus LM with n_lm trial steps.  Returns (units, seconds, description)."""
+    import oracle as O
+    spec = synth.JobSpec(N=N, T=1, F=1, K=1, S=S, f_lo=150e6, f_hi=150e6, seed=seed)
+    uvw, f, sky = synth.station_uvw(spec), synth.freqs(spec), synth.sky(spec)
+    Jt = synth.jones_true(spec)
+    t0 = time.perf_counter()
+    C = O.predict_coherencies(uvw, f, sky.l, sky.m, sky.flux, sky.alpha)
+    V = O.model_vis(C, Jt[0]) + synth.noise(spec)
+    O.lm_cluster(V, C, synth.identity_jones(1, N)[0], n_lm, eps_grad=0.0)
+    dt = time.perf_counter() - t0
+    units = spec.B * spec.T * spec.F * 1 * n_lm
+    desc = ("oracle (numpy FP64) on %d stations x 1 timeslot x 1 channel, 1 cluster x %d sources: "
+            "predict + LM with %d trial step(s); numpy elementwise work single-threaded, "
+            "LAPACK Cholesky on the BLAS thread pool" % (N, S, n_lm))
+    return units, dt, desc
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# --- clocks during the timed region ------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --- our arm ---------------------------------------------------------------------------------------
+
+def make_job(spec, prec, dev):
+    """Device-resident inputs of one job.  The observed visibilities are
+    simulated with the library's own prediction (true Jones, thermal noise);
+    they are inputs here, not results."""
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    uvw = torch.as_tensor(synth.station_uvw(spec)).to(dev)
+    freqs = torch.as_tensor(synth.freqs(spec)).to(dev)
+    sky = synth.sky(spec)
+    dsky = sc.DeviceSky.from_synth(sky, dev)
+    shp = sc.Shape(spec.N, spec.T, spec.F, spec.K, spec.S)
+    ws = sc.workspace(shp, prec, dev)
+    C = sc.predict_coherencies(shp, uvw, freqs, dsky, prec, ws)
+    Jt = torch.as_tensor(synth.jones_true(spec)).to(dev)
+    p, q = np.triu_indices(spec.N, 1)
+    cdt = C.dtype
+    V = torch.zeros((spec.T, spec.B, spec.F, 2, 2), dtype=cdt, device=dev)
+    for k in range(spec.K):
+        G = (Jt[k, p] @ Jt[k, q].conj().transpose(-1, -2)).to(cdt)          # [B][2][2]
+        V += C[k][..., None, None] * G[None, :, None]
+    del C
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234 + spec.seed)
+    rdt = torch.float32 if cdt == torch.complex64 else torch.float64
+    noise = torch.randn((*V.shape, 2), generator=g, device=dev, dtype=rdt) * spec.sigma
+    V += torch.view_as_complex(noise)
+    J0 = torch.as_tensor(synth.identity_jones(spec.K, spec.N)).to(dev)
+    return dict(shape=shp, uvw=uvw, freqs=freqs, sky=dsky, V=V.contiguous(), J0=J0, ws=ws,
+                sky_host=sky)
+
+
+def roofline_for(kind, spec, prec, n_em, n_lm, launches, ms, pk, peak_src):
+    """Algorithmic work of one launch of the dominant kernel kind."""
+    from paper_1910_13908_gb300 import sagecal as sc
+    P = 8 * spec.N
+    Ppad = (P + 63) // 64 * 64
+    vis = spec.B * spec.T * spec.F
+    rs = 4 if prec == sc.SC_MIXED else 8
+    avg_s = (ms / 1e3) / max(launches, 1)
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    if kind == "cholesky":
+        work = P ** 3 / 3.0                         # flops of L L^T = A
+        if prec == sc.SC_MIXED:
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
+            return dict(bound="alu", achieved=work / avg_s / 1e12, peak=peak, unit="TFLOP/s",
+                        peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz)
+        peak = 1.25
+        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=peak, unit="TFLOP/s",
+                    peak_source="FP64 nominal 1.25 TFLOP/s")
+    if kind == "vis_pass":
+        work = vis * (4 * 2 * rs + 2 * rs)               # read residual (2x2 complex) + coherency
+        return dict(bound="hbm", achieved=work / avg_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                    peak_source=peak_src)
+    if kind == "jhj_assemble":
+        work = Ppad * (Ppad + 4) / 2 * rs               # lower triangle written
+        return dict(bound="hbm", achieved=work / avg_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                    peak_source=peak_src)
+    if kind == "tri_solve":
+        work = Ppad * Ppad * rs                          # L read once forward, once backward (half each)
+        return dict(bound="hbm", achieved=work / avg_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                    peak_source=peak_src)
+    if kind == "coherency":
+        work = 8.0 * vis * spec.S                        # one complex multiply-add per (source, vis)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=peak, unit="TFLOP/s",
+                    peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz)
+    return dict(bound="latency", achieved=None, peak=None, unit=None)
+
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/),
+# keyed by (kernel kind, workload); None until captured for the current kernel.
+NCU_TRAFFIC = {}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    sc.lib()
+    cfg, n_em, n_lm, desc = WORKLOADS[args.workload]
+    spec = synth.config(cfg, seed=rank)
+    prec = sc.SC_FP64 if args.prec == "fp64" else sc.SC_MIXED
+    job = make_job(spec, prec, dev)
+    J = job["J0"].clone()
+    costs = torch.zeros((spec.K,), dtype=torch.float64, device=dev)
+    units = spec.B * spec.T * spec.F * spec.K * n_lm * n_em
+
+    def step():
+        J.copy_(job["J0"])
+        sc.calibrate_sage(job["shape"], job["uvw"], job["freqs"], job["sky"], job["V"], J, prec,
+                          job["ws"], n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine, costs=costs)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if sc.device_status(job["ws"]) & 2:
+        raise RuntimeError("device wait timed out during warm-up")
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    n0 = sc.launch_count()
+    sc.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    prof = sc.profile_end()
+    n_launch = sc.launch_count() - n0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * args.steps * world / (ms / 1e3)
+    final_costs = costs.cpu().numpy().tolist()
+
+    # end to end through the public API: host inputs (pinned) -> device -> result back
+    e2e = None
+    if not args.no_e2e:
+        hV = job["V"].cpu().pin_memory()
+        hu, hf = job["uvw"].cpu().pin_memory(), job["freqs"].cpu().pin_memory()
+        hs = {k: getattr(job["sky"], k).cpu().pin_memory() for k in ("l", "m", "flux", "alpha")}
+        hJ0 = job["J0"].cpu().pin_memory()
+        hJ = torch.empty_like(hJ0).pin_memory()
+        hc = torch.empty((spec.K,), dtype=torch.float64).pin_memory()
+        dV, du, df = torch.empty_like(job["V"]), torch.empty_like(job["uvw"]), torch.empty_like(job["freqs"])
+        ds = {k: torch.empty_like(v, device=dev) for k, v in hs.items()}
+        dJ = torch.empty_like(job["J0"])
+        dsky = sc.DeviceSky(ds["l"], ds["m"], ds["flux"], ds["alpha"], job["sky"].offsets, job["sky"].f0)
+        bi = sum(t.numel() * t.element_size() for t in [hV, hu, hf, hJ0, *hs.values()])
+        bo = hJ.numel() * hJ.element_size() + hc.numel() * hc.element_size()
+
+        def e2e_step():
+            dV.copy_(hV, non_blocking=True)
+            du.copy_(hu, non_blocking=True)
+            df.copy_(hf, non_blocking=True)
+            for k in ds:
+                ds[k].copy_(hs[k], non_blocking=True)
+            dJ.copy_(hJ0, non_blocking=True)
+            sc.calibrate_sage(job["shape"], du, df, dsky, dV, dJ, prec, job["ws"], n_em=n_em, n_lm=n_lm,
+                              refine_sweeps=args.refine, costs=costs)
+            hJ.copy_(dJ, non_blocking=True)
+            hc.copy_(costs, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = max(1, min(args.steps, 3))
+        f0.record()
+        for _ in range(ks):
+            e2e_step()
+        f1.record()
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": units * ks * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo), "steps": ks}
+
+    # the plain FP64 GPU path and the mixed path on the same bounded sample
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        fp64 = compare_fp64(spec, dev, args)
+
+    pk, src = peaks()
+    dominant = max(prof, key=lambda k: prof[k][1])
+    n_dom, ms_dom = prof[dominant]
+    roof = roofline_for(dominant, spec, prec, n_em, n_lm, n_dom, ms_dom, pk, src)
+    if roof.get("achieved") is not None and roof.get("peak"):
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dominant
+    roof["launches"] = n_dom
+    roof["avg_launch_us"] = 1e3 * ms_dom / max(n_dom, 1)
+    roof["share_of_step"] = ms_dom / ms if ms > 0 else None
+    roof["traffic"] = NCU_TRAFFIC.get((dominant, args.workload))
+    roof["peak_kind"] = src
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        u, dt, d = oracle_sample(n_lm=2)
+        cpu = {"value": u / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle", "sample": d,
+               "seconds": round(dt, 2)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == sc.SC_MIXED else "f64",
+        "data": "synthetic (seeded stations, sky, Jones and noise shaped like the paper's datasets)",
+        "config": {"workload": args.workload, "description": desc, "stations": spec.N,
+                   "baselines": spec.B, "timeslots": spec.T, "channels": spec.F, "clusters": spec.K,
+                   "sources_per_cluster": spec.S, "n_em": n_em, "n_lm": n_lm,
+                   "refine_sweeps": args.refine if prec == sc.SC_MIXED else 0,
+                   "precision": args.prec, "parallelism": "one independent job per GPU (replicas)",
+                   "l2": "inputs larger than L2 (coherency cache %.2f GB + visibilities %.2f GB per job)"
+                         % (spec.K * spec.T * spec.B * spec.F * (8 if prec == sc.SC_MIXED else 16) / 1e9,
+                            spec.T * spec.B * spec.F * (32 if prec == sc.SC_MIXED else 64) / 1e9)},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(n_launch),
+        "clocks": clk,
+        "fp64_gpu": fp64,
+        "kernel_ms": breakdown,
+        "final_costs_head": final_costs[:4],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def compare_fp64(spec, dev, args):
+    """vis.cluster/s per LM iteration of the plain FP64 GPU path and of the
+    mixed path on one bounded sample of the same job: all stations,
+    timeslots and channels, one cluster, one SAGE sweep of 10 LM iterations."""
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    sub = synth.JobSpec(**{**spec.__dict__, "K": 1})
+    out = {}
+    for name, prec in (("fp64", sc.SC_FP64), ("mixed", sc.SC_MIXED)):
+        job = make_job(sub, prec, dev)
+        J = job["J0"].clone()
+
+        def go():
+            J.copy_(job["J0"])
+            sc.calibrate_sage(job["shape"], job["uvw"], job["freqs"], job["sky"], job["V"], J, prec, job["ws"],
+                              n_em=1, n_lm=10, refine_sweeps=args.refine)
+        go()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        go()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = sub.B * sub.T * sub.F * 10 / (e0.elapsed_time(e1) / 1e3)
+        del job
+        torch.cuda.empty_cache()
+    return {"value": out["fp64"], "unit": UNIT, "mixed_same_sample": out["mixed"],
+            "speedup_mixed_over_fp64": out["mixed"] / out["fp64"],
+            "sample": "%d stations x %d timeslots x %d channels, 1 cluster x %d sources, 1 sweep x 10 LM "
+                      "(predict included)" % (sub.N, sub.T, sub.F, sub.S)}
+
+
+# --- reference arm: the FP64 CPU oracle -------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg, n_em, n_lm, desc = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(n_lm=1)
+    tot_u, tot_t, d = 0, 0.0, ""
+    for _ in range(args.steps):
+        u, dt, d = oracle_sample(n_lm=1)
+        tot_u += u
+        tot_t += dt
+    value = tot_u / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": host_cores(), "sample": d},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ska512", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--refine", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle sample")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * sagecal_gb.h -- C ABI of the GB300 SAGE/EM direction-dependent calibration
+ * hot path (Spreeuw, van Werkhoven, Yatawatta & Diblen, "GPU acceleration of
+ * the SAGECal calibration package for the SKA", arXiv:1910.13908).
+ *
+ * The paper times SAGECal calibrating a sky model grouped into clusters, one
+ * solution per cluster (paper §2), on arrays of N stations whose data grow as
+ * the N(N-1)/2 baselines (§3).  The arithmetic it times is SAGECal's:
+ *
+ *   measurement equation   V_pq = sum_k J_kp C_kpq J_kq^H + noise
+ *   point-source coherency C_pq(t,f) = sum_s S_s(f)
+ *                              exp(-2 pi i f/c (u l_s + v m_s + w (n_s - 1))) Id
+ *   per cluster            Levenberg-Marquardt on the normal equations
+ *                          (J^T J + mu diag(J^T J)) d = J^T r, solved by a
+ *                          dense Cholesky factorisation (8N x 8N)
+ *   across clusters        SAGE/EM: each cluster solved in turn against the
+ *                          data minus the other clusters' current models.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Baselines b = (p, q), p < q, b = p*N - p(p+1)/2 + (q-p-1); B = N(N-1)/2.
+ *    Autocorrelations are not stored; the q<p baseline is the Hermitian
+ *    conjugate of the p<q one.
+ *  - Station coordinates uvw: float64 [T][N][3] metres; the (u,v,w) of
+ *    baseline pq is uvw_p - uvw_q.
+ *  - Visibilities (V, X, R): [T][B][F][2][2] complex, row-major 2x2
+ *    (XX, XY, YX, YY), interleaved (re, im): complex64 for SC_MIXED,
+ *    complex128 for SC_FP64.
+ *  - Coherencies C: [T][B][F] complex (same element type as the
+ *    visibilities).  The brightness of an unpolarised point source is a
+ *    multiple of the identity, so one complex number per (t, b, f) is the
+ *    whole 2x2 coherency c * Id.
+ *  - Jones: complex128 [N][2][2] per cluster (always FP64: it is the solver
+ *    state); the 8 real parameters of station s are
+ *    theta[8s + 4i + 2j + 0/1] = Re/Im J_s[i][j], which is exactly the
+ *    memory order of the complex128 array.
+ *  - J^T J: [8N][8N] row-major, float (SC_MIXED) or double (SC_FP64);
+ *    J^T r: double [8N], with r = X - model, so the LM step solves
+ *    (J^T J + mu diag(J^T J)) d = J^T r.
+ *
+ * Memory and streams
+ * ------------------
+ *  All array pointers are DEVICE pointers owned by the caller unless marked
+ *  HOST.  The library allocates no memory: every call that needs scratch
+ *  takes a caller-owned device workspace (ws, ws_bytes) of at least
+ *  sc_workspace_size() bytes, 256-byte aligned.  Every compute call is
+ *  asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream);
+ *  outputs are valid once the stream has reached that point.  Calls that
+ *  share one workspace must not overlap on the device.
+ *
+ * Errors
+ * ------
+ *  Every call returns SC_OK (0) or a negative SC_E* code, with a message
+ *  retrievable by sc_last_error() (thread-local).  Argument errors are
+ *  detected on the host before anything is launched.  Conditions found on
+ *  the device (a non-positive-definite damped matrix, a bounded wait that
+ *  gave up) are recorded in a status word inside the workspace and returned
+ *  by sc_device_status() after the stream has been synchronised.  No call
+ *  throws, traps or aborts.
+ */
+#ifndef SAGECAL_GB_H
+#define SAGECAL_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SC_API __attribute__((visibility("default")))
+#else
+#define SC_API
+#endif
+
+#define SC_OK 0
+#define SC_EINVAL (-1)   /* bad shape, null pointer, N < 2, unknown precision */
+#define SC_ENOMEM (-2)   /* workspace smaller than sc_workspace_size() */
+#define SC_ENOTPD (-3)   /* damped J^T J not positive definite (device status) */
+#define SC_ETIMEOUT (-4) /* a bounded device wait gave up (device status) */
+#define SC_ECUDA (-5)    /* a CUDA runtime call failed */
+
+/* Device status bits (sc_device_status) */
+#define SC_STATUS_NOTPD 1u
+#define SC_STATUS_TIMEOUT 2u
+
+typedef enum sc_precision {
+  SC_FP64 = 0,  /* everything in float64 / complex128 */
+  SC_MIXED = 1  /* float32 data and factorisation, float64 phase argument,
+                   float64 Jones state and iterative refinement of the step */
+} sc_precision;
+
+/* Shape of one calibration job (one sub-band x time chunk). */
+typedef struct sc_dims {
+  int32_t N;     /* stations, >= 2 */
+  int32_t T;     /* timeslots, >= 1 */
+  int32_t F;     /* channels, >= 1 */
+  int32_t K;     /* clusters (calibration directions), >= 1 */
+  int32_t S_max; /* most sources in any one cluster (>= 1 for calls that predict) */
+} sc_dims;
+
+/* Clustered point-source sky model (paper §2: contiguous sources grouped
+ * into clusters).  Sources of cluster k are [offsets[k], offsets[k+1]). */
+typedef struct sc_sky {
+  const int32_t* offsets; /* HOST [K+1], offsets[0] = 0, non-decreasing */
+  const double* l;        /* DEVICE [S_total] direction cosine towards east */
+  const double* m;        /* DEVICE [S_total] direction cosine towards north */
+  const double* flux;     /* DEVICE [S_total] Stokes I flux density at f0, Jy */
+  const double* alpha;    /* DEVICE [S_total] spectral index, S(f) = flux (f/f0)^alpha */
+  double f0;              /* reference frequency, Hz */
+} sc_sky;
+
+/* Levenberg-Marquardt options (Madsen, Nielsen & Tingleff 2004, Alg. 3.16
+ * with Marquardt's scaling D = diag(J^T J)). */
+typedef struct sc_lm_opts {
+  int32_t n_lm;          /* trial steps per solve, accepted or rejected */
+  int32_t refine_sweeps; /* SC_MIXED: float64 iterative-refinement sweeps of
+                            each float32 Cholesky solve (ignored for SC_FP64) */
+  double tau;            /* mu0 = tau * max diag(J^T J) */
+  double eps_grad;       /* stop once max|J^T r| <= eps_grad * (1 + cost) */
+} sc_lm_opts;
+
+typedef struct sc_sage_opts {
+  int32_t n_em; /* SAGE/EM sweeps over all clusters */
+  sc_lm_opts lm;
+} sc_sage_opts;
+
+/* Library version, (major << 16) | minor. */
+SC_API int32_t sc_version(void);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len).  Returns the last error code. */
+SC_API int32_t sc_last_error(char* buf, size_t len);
+
+/* Bytes of device workspace that every call below needs for shape d at
+ * precision prec (SC_FP64 / SC_MIXED).  Writes *bytes. */
+SC_API int32_t sc_workspace_size(const sc_dims* d, int32_t prec, size_t* bytes);
+
+/* After synchronising the stream of the last call that used ws: the device
+ * status word (SC_STATUS_* bits, 0 = clean) of that workspace, which is
+ * cleared by every call that launches work on it. */
+SC_API int32_t sc_device_status(const void* ws, size_t ws_bytes, uint32_t* status);
+
+/* Diagnostic, host only (launches nothing): the task order of the tiled
+ * Cholesky factorisation (which = 0) or of the two triangular solves
+ * (which = 1) on an nT x nT grid of 64x64 tiles, as (type, i, k, j)
+ * quadruples written to out[0 .. 4*cap).  Types: 0 POTRF(j), 1 TRSM(i, j),
+ * 2 UPDATE(i, k, j), 3 forward solve of tile row i, 4 backward solve of tile
+ * row i.  With out = NULL only counts.  Returns the number of tasks, or a
+ * negative SC_E* code. */
+SC_API int32_t sc_chol_schedule(int32_t nT, int32_t which, int32_t* out, int32_t cap);
+
+/* Diagnostics.  sc_launch_count: kernels launched by this library since it
+ * was loaded (all threads).  sc_profile_begin / sc_profile_end: while
+ * profiling is on, every kernel launch is bracketed by two CUDA events on its
+ * stream (a few microseconds each); sc_profile_end waits for them and
+ * sc_profile_read returns, per kernel kind, the launches and their summed
+ * device time in ms.  Kinds: 0 station phasors, 1 coherency contraction /
+ * FP64 direct predict, 2 visibility pass, 3 station reduction, 4 J^T J
+ * assembly, 5 Cholesky factorisation, 6 triangular solves, 7 refinement
+ * residual, 8 LM control, 9 other helpers. */
+SC_API uint64_t sc_launch_count(void);
+SC_API int32_t sc_profile_begin(void);
+SC_API int32_t sc_profile_end(void);
+SC_API int32_t sc_profile_read(int32_t kind, int64_t* launches, double* total_ms);
+
+/* Step (a): point-source coherencies of every cluster.
+ *   uvw   DEVICE float64 [T][N][3] station coordinates, metres
+ *   freqs DEVICE float64 [F] channel frequencies, Hz
+ *   sky   clustered sky model (offsets on the HOST, K = d->K clusters)
+ *   C     DEVICE out [K][T][B][F] complex (complex64 SC_MIXED, complex128 SC_FP64)
+ * SC_FP64 evaluates every (source, baseline, timeslot, channel) phase in
+ * float64.  SC_MIXED forms each station's phasor exp(-2 pi i f/c uvw_p.s)
+ * from a float64 argument reduced to [-1/2, 1/2) turns, evaluates it in
+ * float32 and multiplies station phasors (baseline phase = difference of
+ * station phases, exact for point sources), accumulating in float32. */
+SC_API int32_t sc_predict_coherencies(const sc_dims* d, const double* uvw,
+                                      const double* freqs, const sc_sky* sky,
+                                      void* C, int32_t prec, void* ws,
+                                      size_t ws_bytes, void* stream);
+
+/* Step (b): residual of one cluster, R = X - J_p (c Id) J_q^H, and its cost
+ * sum |R|_F^2.
+ *   X     DEVICE [T][B][F][2][2] complex data
+ *   C     DEVICE [T][B][F] complex coherencies of the cluster
+ *   jones DEVICE complex128 [N][2][2]
+ *   R     DEVICE out, same layout as X; may equal X (in place); may be NULL
+ *   cost  DEVICE out float64 scalar; may be NULL */
+SC_API int32_t sc_residual(const sc_dims* d, const void* X, const void* C,
+                           const double* jones, void* R, double* cost,
+                           int32_t prec, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* Step (c): Gauss-Newton normal equations of one cluster at residual R
+ * (= X - model at `jones`):
+ *   JhJ   DEVICE out [8N][8N] row-major, float (SC_MIXED) / double (SC_FP64),
+ *         the undamped J^T J, both triangles written
+ *   Jhr   DEVICE out float64 [8N], J^T r
+ * For an unpolarised sky J^T J depends on the data only through
+ * w_pq = sum_{t,f} |c_pq(t,f)|^2, which is summed here from C. */
+SC_API int32_t sc_lm_normal_eqs(const sc_dims* d, const void* R, const void* C,
+                                const double* jones, void* JhJ, double* Jhr,
+                                int32_t prec, void* ws, size_t ws_bytes,
+                                void* stream);
+
+/* Steps (b)-(c) iterated: Levenberg-Marquardt solve of one cluster against
+ * data X, warm-started from and overwriting `jones` (complex128 [N][2][2]).
+ *   cost  DEVICE out float64 scalar, final sum |X - model|^2
+ *   iters DEVICE out int32 scalar, trial steps taken (<= n_lm)
+ * Every iteration stays on the device: the damped J^T J is assembled,
+ * factorised by a blocked Cholesky (float32 + float64 refinement for
+ * SC_MIXED, float64 for SC_FP64), the step is tried and accepted or rejected
+ * by the gain ratio without a host round trip.  A damped matrix that is not
+ * positive definite counts as a rejected step (and sets SC_STATUS_NOTPD). */
+SC_API int32_t sc_solve_cluster(const sc_dims* d, const void* X, const void* C,
+                                double* jones, const sc_lm_opts* opts,
+                                double* cost, int32_t* iters, int32_t prec,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/* The whole path for one job: predict every cluster, then n_em SAGE sweeps;
+ * in each, cluster k = 0..K-1 is solved by LM against
+ * X_k = V - sum_{j != k} model_j, kept as a running residual of all
+ * clusters plus model_k.
+ *   V      DEVICE [T][B][F][2][2] complex observed visibilities
+ *   jones  DEVICE complex128 [K][N][2][2], initial guess in, solution out
+ *   costs  DEVICE out float64 [K], final LM cost of each cluster in the last
+ *          sweep */
+SC_API int32_t sc_calibrate_sage(const sc_dims* d, const double* uvw,
+                                 const double* freqs, const sc_sky* sky,
+                                 const void* V, double* jones,
+                                 const sc_sage_opts* opts, double* costs,
+                                 int32_t prec, void* ws, size_t ws_bytes,
+                                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAGECAL_GB_H */

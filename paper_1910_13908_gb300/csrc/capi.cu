@@ -1,0 +1,475 @@
+// The C ABI (include/sagecal_gb.h): argument checks, workspace layout, and the
+// host-side sequencing of the kernels for one cluster solve and for a SAGE
+// job.  Everything is enqueued on the caller's stream; no call synchronises,
+// allocates or round-trips to the host between kernels.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "sc_common.cuh"
+
+namespace sc {
+
+// ---- errors --------------------------------------------------------------------------------
+
+static thread_local int g_err = SC_OK;
+static thread_local char g_msg[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  g_err = code;
+  return code;
+}
+static int ok() {
+  g_err = SC_OK;
+  g_msg[0] = 0;
+  return SC_OK;
+}
+
+#define SC_CUDA(expr)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) return fail(SC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// one kernel launch of kind K on stream c.st, timed when profiling is on
+#define SC_LAUNCH(K, expr)                                                                 \
+  do {                                                                                     \
+    prof_start(K, c.st);                                                                   \
+    cudaError_t e_ = (expr);                                                               \
+    prof_stop(K, c.st);                                                                    \
+    if (e_ != cudaSuccess) return fail(SC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---- workspace layout ----------------------------------------------------------------------
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Workspace plan_workspace(const Shape& s, bool job) {
+  Workspace L{};
+  size_t rs = s.prec == SC_MIXED ? 4 : 8;
+  size_t N = s.N, T = s.T, F = s.F, K = s.K, B = (size_t)s.B;
+  size_t Smax = std::max(s.S_max, 1);
+  L.Ppad = (int)((8 * N + kNB - 1) / kNB * kNB);
+  L.nT = L.Ppad / kNB;
+  // enough (baseline, timeslot-chunk) work items to fill the GPU several times
+  const int64_t target = 1 << 18;
+  int64_t tb = (int64_t)T * (int64_t)B;
+  L.tchunk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)T, tb / target));
+  L.nchunk = (int)((T + L.tchunk - 1) / L.tchunk);
+  int nt = (s.N + 63) / 64, tiles = nt * (nt + 1) / 2;
+  L.splits = std::max(1, std::min(s.T * s.F, (2 * 152 + tiles - 1) / tiles));
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  L.status = take(256);
+  L.lm = take(sizeof(LMState));
+  L.C = job ? take(K * T * B * F * 2 * rs) : 0;
+  L.w = take((job ? K : 1) * B * rs);
+  L.wpart = take((size_t)L.splits * B * 4);
+  L.Rres = job ? take(T * B * F * 8 * rs) : 0;
+  L.E = s.prec == SC_MIXED ? take(T * F * Smax * N * 8) : 0;
+  L.Sf = take(F * Smax * 8);
+  L.stat_cost = take((size_t)L.nchunk * B * rs);
+  L.stat_rho = take((size_t)L.nchunk * B * 8 * rs);
+  L.J_old = take(8 * N * 8);
+  L.J_cur = take(8 * N * 8);
+  L.J_trial = take(8 * N * 8);
+  L.g_cur = take(8 * N * 8);
+  L.g_trial = take(8 * N * 8);
+  L.H_cur = take(4 * N * 8);
+  L.H_trial = take(4 * N * 8);
+  L.cpart_cur = take(N * 8);
+  L.cpart_trial = take(N * 8);
+  L.x = take((size_t)L.Ppad * 8);
+  L.rvec = take((size_t)L.Ppad * 8);
+  L.corr = take((size_t)L.Ppad * 8);
+  L.bvec = take((size_t)L.Ppad * rs);
+  L.A = take((size_t)L.Ppad * L.Ppad * rs);
+  L.Linv = take((size_t)L.nT * kNB * kNB * rs);
+  L.sync = take((size_t)chol_sync_ints(L.nT) * 4);
+  L.total = o;
+  return L;
+}
+
+// ---- argument checks -----------------------------------------------------------------------
+
+static int check_dims(const sc_dims* d, int32_t prec, Shape& s) {
+  if (d == nullptr) return fail(SC_EINVAL, "dims is NULL");
+  if (prec != SC_FP64 && prec != SC_MIXED) return fail(SC_EINVAL, "unknown precision %d", prec);
+  if (d->N < 2 || d->N > 8000) return fail(SC_EINVAL, "N = %d outside [2, 8000]", d->N);
+  if (d->T < 1 || d->F < 1 || d->K < 1) return fail(SC_EINVAL, "T, F, K must be >= 1 (T=%d F=%d K=%d)", d->T, d->F, d->K);
+  if ((int64_t)d->T * d->F > 65535) return fail(SC_EINVAL, "T*F = %lld exceeds 65535", (long long)d->T * d->F);
+  if (d->S_max < 0 || d->S_max > 65535) return fail(SC_EINVAL, "S_max = %d outside [0, 65535]", d->S_max);
+  s.N = d->N;
+  s.T = d->T;
+  s.F = d->F;
+  s.K = d->K;
+  s.S_max = d->S_max;
+  s.B = (int64_t)d->N * (d->N - 1) / 2;
+  s.prec = prec;
+  return SC_OK;
+}
+
+struct Ctx {
+  Shape s;
+  Workspace L;
+  char* base;
+  cudaStream_t st;
+  template <class T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(base + off);
+  }
+  uint32_t* status() const { return at<uint32_t>(L.status); }
+  LMState* lm() const { return at<LMState>(L.lm); }
+};
+
+static int open_ctx(Ctx& c, const sc_dims* d, int32_t prec, void* ws, size_t ws_bytes, void* stream) {
+  int r = check_dims(d, prec, c.s);
+  if (r) return r;
+  if (ws == nullptr) return fail(SC_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(SC_EINVAL, "workspace not 256-byte aligned");
+  c.L = plan_workspace(c.s, true);
+  if (ws_bytes < c.L.total)
+    return fail(SC_ENOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, c.L.total);
+  c.base = static_cast<char*>(ws);
+  c.st = static_cast<cudaStream_t>(stream);
+  SC_CUDA(cudaMemsetAsync(c.status(), 0, 256, c.st));
+  return SC_OK;
+}
+
+static int check_sky(const Shape& s, const sc_sky* sky) {
+  if (sky == nullptr || sky->offsets == nullptr) return fail(SC_EINVAL, "sky or sky->offsets is NULL");
+  if (sky->offsets[0] != 0) return fail(SC_EINVAL, "sky->offsets[0] must be 0");
+  for (int k = 0; k < s.K; ++k) {
+    int n = sky->offsets[k + 1] - sky->offsets[k];
+    if (n < 0) return fail(SC_EINVAL, "sky->offsets decreases at cluster %d", k);
+    if (n > s.S_max) return fail(SC_EINVAL, "cluster %d has %d sources > S_max = %d", k, n, s.S_max);
+  }
+  if (sky->offsets[s.K] > 0 && (!sky->l || !sky->m || !sky->flux || !sky->alpha))
+    return fail(SC_EINVAL, "sky source arrays must not be NULL");
+  if (!(sky->f0 > 0)) return fail(SC_EINVAL, "sky->f0 must be > 0");
+  return SC_OK;
+}
+
+static int check_lm(const sc_lm_opts* o) {
+  if (o == nullptr) return fail(SC_EINVAL, "LM options are NULL");
+  if (o->n_lm < 0 || o->refine_sweeps < 0 || o->refine_sweeps > 16)
+    return fail(SC_EINVAL, "n_lm must be >= 0 and refine_sweeps in [0, 16]");
+  if (!(o->tau > 0)) return fail(SC_EINVAL, "tau must be > 0");
+  if (!(o->eps_grad >= 0)) return fail(SC_EINVAL, "eps_grad must be >= 0");
+  return SC_OK;
+}
+
+// ---- pieces of the path ----------------------------------------------------------------------
+
+// Coherencies of every cluster into C_out [K][T][B][F]; w_out [K][B] if not NULL.
+template <typename R>
+static int predict_all(const Ctx& c, const double* uvw, const double* freqs, const sc_sky* sky,
+                       R* C_out, R* w_out) {
+  const Shape& s = c.s;
+  size_t per = (size_t)s.T * s.B * s.F * 2;
+  for (int k = 0; k < s.K; ++k) {
+    int a = sky->offsets[k], S = sky->offsets[k + 1] - a;
+    R* Ck = C_out + per * k;
+    if (s.prec == SC_MIXED) {
+      float2* E = c.at<float2>(c.L.E);
+      float* Sf = c.at<float>(c.L.Sf);
+      float* wpart = c.at<float>(c.L.wpart);
+      SC_LAUNCH(PK_PHASORS, launch_station_phasors(s, uvw, freqs, sky->l + a, sky->m + a, sky->flux + a,
+                                     sky->alpha + a, sky->f0, S, E, Sf, c.st));
+      SC_LAUNCH(PK_COHERENCY, launch_coherency_f32(s, S, E, Sf, reinterpret_cast<float2*>(Ck), wpart, c.L.splits, c.st));
+      if (w_out)
+        SC_LAUNCH(PK_OTHER, launch_sum_parts(wpart, c.L.splits, s.B, reinterpret_cast<float*>(w_out) + (size_t)s.B * k,
+                                 c.st));
+    } else {
+      if (S > 0) {
+        SC_LAUNCH(PK_COHERENCY, launch_predict_f64(s, uvw, freqs, sky->l + a, sky->m + a, sky->flux + a, sky->alpha + a,
+                                   sky->f0, S, reinterpret_cast<double2*>(Ck), c.st));
+      } else {
+        SC_CUDA(cudaMemsetAsync(Ck, 0, per * sizeof(R), c.st));
+      }
+      if (w_out)
+        SC_LAUNCH(PK_OTHER, launch_w_from_C<R>(s, Ck, w_out + (size_t)s.B * k, c.st));
+    }
+  }
+  return SC_OK;
+}
+
+// Levenberg-Marquardt on one cluster.  Data: X = Xin (running = false) or
+// X = Xin + c J_old J_old^H with J_old the Jones at entry (running = true,
+// Xin being the residual of all clusters).  J_io [8N] in/out.
+template <typename R>
+static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const R* w, double* J_io,
+                    const sc_lm_opts& o, double* cost_out, int32_t* iters_out) {
+  const Shape& s = c.s;
+  const Workspace& L = c.L;
+  size_t n8 = (size_t)8 * s.N * sizeof(double);
+  double* J_old = c.at<double>(L.J_old);
+  double* J_cur = c.at<double>(L.J_cur);
+  double* J_trial = c.at<double>(L.J_trial);
+  double* g_cur = c.at<double>(L.g_cur);
+  double* g_trial = c.at<double>(L.g_trial);
+  double* H_cur = c.at<double>(L.H_cur);
+  double* H_trial = c.at<double>(L.H_trial);
+  double* cp_cur = c.at<double>(L.cpart_cur);
+  double* cp_trial = c.at<double>(L.cpart_trial);
+  double* x = c.at<double>(L.x);
+  double* rvec = c.at<double>(L.rvec);
+  R* stc = c.at<R>(L.stat_cost);
+  R* str = c.at<R>(L.stat_rho);
+  R* A = c.at<R>(L.A);
+  R* Linv = c.at<R>(L.Linv);
+  R* bw = c.at<R>(L.bvec);
+  int* sync = c.at<int>(L.sync);
+  LMState* lm = c.lm();
+  const int flags = running ? (P_OLD | P_SUB | P_STATS) : (P_SUB | P_STATS);
+  const bool mixed = s.prec == SC_MIXED;
+
+  SC_CUDA(cudaMemcpyAsync(J_old, J_io, n8, cudaMemcpyDeviceToDevice, c.st));
+  SC_CUDA(cudaMemcpyAsync(J_cur, J_io, n8, cudaMemcpyDeviceToDevice, c.st));
+  SC_CUDA(cudaMemsetAsync(x, 0, (size_t)L.Ppad * sizeof(double), c.st));
+  SC_CUDA(cudaMemsetAsync(rvec, 0, (size_t)L.Ppad * sizeof(double), c.st));
+  SC_LAUNCH(PK_PASS, launch_pass<R>(s, flags, Xin, C, J_old, J_cur, nullptr, stc, str, L.nchunk, L.tchunk, nullptr, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_cur, g_cur, H_cur, cp_cur, nullptr, c.st));
+  SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, H_cur, g_cur, cp_cur, J_cur, J_cur, c.st));
+  for (int it = 0; it < o.n_lm; ++it) {
+    SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, J_cur, H_cur, lm, A, true, false, c.st));
+    SC_LAUNCH(PK_CHOL, launch_chol<R>(A, L.Ppad, L.nT, Linv, sync, c.status(), lm, c.st));
+    SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, g_cur, bw, x, 0, c.status(), lm, c.st));
+    if (mixed) {
+      for (int sw = 0; sw < o.refine_sweeps; ++sw) {
+        SC_LAUNCH(PK_REFINE, launch_refine_residual<R>(s, w, J_cur, H_cur, g_cur, x, lm, rvec, c.st));
+        SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, rvec, bw, x, 1, c.status(), lm, c.st));
+      }
+    }
+    SC_LAUNCH(PK_LM, launch_lm_trial(lm, s.N, L.Ppad, J_cur, x, H_cur, g_cur, J_trial, c.st));
+    SC_LAUNCH(PK_PASS, launch_pass<R>(s, flags, Xin, C, J_old, J_trial, nullptr, stc, str, L.nchunk, L.tchunk, lm, c.st));
+    SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_trial, g_trial, H_trial, cp_trial, lm, c.st));
+    SC_LAUNCH(PK_LM, launch_lm_decide(lm, s.N, cp_trial, J_cur, J_trial, g_cur, g_trial, H_cur, H_trial, c.st));
+  }
+  SC_LAUNCH(PK_LM, launch_lm_finish(lm, J_cur, s.N, J_io, cost_out, iters_out, c.st));
+  return SC_OK;
+}
+
+template <typename R>
+static int sage(const Ctx& c, const double* uvw, const double* freqs, const sc_sky* sky, const R* V,
+                double* jones, const sc_sage_opts& o, double* costs) {
+  const Shape& s = c.s;
+  const Workspace& L = c.L;
+  R* C = c.at<R>(L.C);
+  R* w = c.at<R>(L.w);
+  R* Rres = c.at<R>(L.Rres);
+  size_t perC = (size_t)s.T * s.B * s.F * 2;
+  size_t perV = (size_t)s.T * s.B * s.F * 8;
+  int r = predict_all<R>(c, uvw, freqs, sky, C, w);
+  if (r) return r;
+  // running residual R = V - sum_k model_k
+  SC_CUDA(cudaMemcpyAsync(Rres, V, perV * sizeof(R), cudaMemcpyDeviceToDevice, c.st));
+  for (int k = 0; k < s.K; ++k)
+    SC_LAUNCH(PK_PASS, launch_pass<R>(s, P_SUB | P_WRITE_R, Rres, C + perC * k, nullptr, jones + (size_t)8 * s.N * k, Rres,
+                           nullptr, nullptr, L.nchunk, L.tchunk, nullptr, c.st));
+  for (int em = 0; em < o.n_em; ++em) {
+    for (int k = 0; k < s.K; ++k) {
+      double* Jk = jones + (size_t)8 * s.N * k;
+      const R* Ck = C + perC * k;
+      r = lm_solve<R>(c, Rres, true, Ck, w + (size_t)s.B * k, Jk, o.lm, costs ? costs + k : nullptr, nullptr);
+      if (r) return r;
+      // R += c (J_old J_old^H - J_new J_new^H)
+      SC_LAUNCH(PK_PASS, launch_pass<R>(s, P_OLD | P_SUB | P_WRITE_R, Rres, Ck, c.at<double>(L.J_old), Jk, Rres, nullptr,
+                             nullptr, L.nchunk, L.tchunk, nullptr, c.st));
+    }
+  }
+  return SC_OK;
+}
+
+template <typename R>
+static int residual_impl(const Ctx& c, const void* X, const void* C, const double* jones, void* Rout,
+                         double* cost) {
+  const Workspace& L = c.L;
+  int flags = P_SUB | (Rout ? P_WRITE_R : 0) | (cost ? P_STATS : 0);
+  if (!(flags & (P_WRITE_R | P_STATS))) return SC_OK;
+  if (flags == (P_SUB | P_STATS)) {
+    SC_LAUNCH(PK_PASS, launch_pass<R>(c.s, P_SUB | P_STATS, static_cast<const R*>(X), static_cast<const R*>(C), nullptr, jones,
+                           nullptr, c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, L.tchunk, nullptr, c.st));
+  } else {
+    SC_LAUNCH(PK_PASS, launch_pass<R>(c.s, flags, static_cast<const R*>(X), static_cast<const R*>(C), nullptr, jones,
+                           static_cast<R*>(Rout), c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, L.tchunk,
+                           nullptr, c.st));
+  }
+  if (cost) SC_LAUNCH(PK_OTHER, launch_sum_reals<R>(c.at<R>(L.stat_cost), (int64_t)L.nchunk * c.s.B, cost, c.st));
+  return SC_OK;
+}
+
+template <typename R>
+static int normal_eqs_impl(const Ctx& c, const void* Rv, const void* C, const double* jones, void* JhJ,
+                           double* Jhr) {
+  const Workspace& L = c.L;
+  const Shape& s = c.s;
+  R* w = c.at<R>(L.w);
+  SC_LAUNCH(PK_OTHER, launch_w_from_C<R>(s, static_cast<const R*>(C), w, c.st));
+  SC_LAUNCH(PK_PASS, launch_pass<R>(s, P_STATS, static_cast<const R*>(Rv), static_cast<const R*>(C), nullptr, nullptr, nullptr,
+                         c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, L.tchunk, nullptr, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, w, jones, Jhr,
+                                   c.at<double>(L.H_cur), c.at<double>(L.cpart_cur), nullptr, c.st));
+  int P = 8 * s.N;
+  SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, P, P, w, jones, c.at<double>(L.H_cur), nullptr, static_cast<R*>(JhJ), false, true,
+                             c.st));
+  return SC_OK;
+}
+
+}  // namespace sc
+
+using namespace sc;
+
+// ---- exported entry points ------------------------------------------------------------------
+
+extern "C" {
+
+SC_API int32_t sc_version(void) { return (1 << 16) | 0; }
+
+SC_API int32_t sc_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    strncpy(buf, g_msg, len - 1);
+    buf[len - 1] = 0;
+  }
+  return g_err;
+}
+
+SC_API int32_t sc_workspace_size(const sc_dims* d, int32_t prec, size_t* bytes) {
+  Shape s;
+  int r = check_dims(d, prec, s);
+  if (r) return r;
+  if (!bytes) return fail(SC_EINVAL, "bytes is NULL");
+  *bytes = plan_workspace(s, true).total;
+  return ok();
+}
+
+SC_API int32_t sc_device_status(const void* ws, size_t ws_bytes, uint32_t* status) {
+  if (!ws || !status || ws_bytes < 256) return fail(SC_EINVAL, "bad workspace or status pointer");
+  // the status word is at offset 0 of every workspace layout
+  SC_CUDA(cudaMemcpy(status, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  return ok();
+}
+
+SC_API uint64_t sc_launch_count(void) { return launch_count(); }
+
+SC_API int32_t sc_profile_begin(void) {
+  prof_begin();
+  return ok();
+}
+
+SC_API int32_t sc_profile_end(void) {
+  if (prof_end() != 0) return fail(SC_ECUDA, "profiling events could not be read");
+  return ok();
+}
+
+SC_API int32_t sc_profile_read(int32_t kind, int64_t* launches, double* total_ms) {
+  if (kind < 0 || kind >= PK_COUNT || !launches || !total_ms) return fail(SC_EINVAL, "bad profile query");
+  long n = 0;
+  double ms = 0;
+  prof_read(kind, &n, &ms);
+  *launches = n;
+  *total_ms = ms;
+  return ok();
+}
+
+SC_API int32_t sc_chol_schedule(int32_t nT, int32_t which, int32_t* out, int32_t cap) {
+  if (nT < 1 || nT > 1024 || (which != 0 && which != 1)) return fail(SC_EINVAL, "bad nT or list");
+  int n = which == 0 ? chol_ntasks(nT) : 2 * nT;
+  if (out) {
+    if (cap < n) return fail(SC_EINVAL, "capacity %d < %d tasks", cap, n);
+    for (int t = 0; t < n; ++t) {
+      int4 v = which == 0 ? chol_task(nT, t) : solve_task(nT, t);
+      out[4 * t] = v.x;
+      out[4 * t + 1] = v.y;
+      out[4 * t + 2] = v.z;
+      out[4 * t + 3] = v.w;
+    }
+  }
+  ok();
+  return n;
+}
+
+SC_API int32_t sc_predict_coherencies(const sc_dims* d, const double* uvw, const double* freqs,
+                                      const sc_sky* sky, void* C, int32_t prec, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  Ctx c;
+  int r = open_ctx(c, d, prec, ws, ws_bytes, stream);
+  if (r) return r;
+  if ((r = check_sky(c.s, sky))) return r;
+  if (!uvw || !freqs || !C) return fail(SC_EINVAL, "uvw, freqs and C must not be NULL");
+  r = prec == SC_MIXED ? predict_all<float>(c, uvw, freqs, sky, static_cast<float*>(C), nullptr)
+                       : predict_all<double>(c, uvw, freqs, sky, static_cast<double*>(C), nullptr);
+  return r ? r : ok();
+}
+
+SC_API int32_t sc_residual(const sc_dims* d, const void* X, const void* C, const double* jones, void* R,
+                           double* cost, int32_t prec, void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  int r = open_ctx(c, d, prec, ws, ws_bytes, stream);
+  if (r) return r;
+  if (!X || !C || !jones) return fail(SC_EINVAL, "X, C and jones must not be NULL");
+  r = prec == SC_MIXED ? residual_impl<float>(c, X, C, jones, R, cost)
+                       : residual_impl<double>(c, X, C, jones, R, cost);
+  return r ? r : ok();
+}
+
+SC_API int32_t sc_lm_normal_eqs(const sc_dims* d, const void* R, const void* C, const double* jones, void* JhJ,
+                                double* Jhr, int32_t prec, void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  int r = open_ctx(c, d, prec, ws, ws_bytes, stream);
+  if (r) return r;
+  if (!R || !C || !jones || !JhJ || !Jhr) return fail(SC_EINVAL, "R, C, jones, JhJ and Jhr must not be NULL");
+  r = prec == SC_MIXED ? normal_eqs_impl<float>(c, R, C, jones, JhJ, Jhr)
+                       : normal_eqs_impl<double>(c, R, C, jones, JhJ, Jhr);
+  return r ? r : ok();
+}
+
+SC_API int32_t sc_solve_cluster(const sc_dims* d, const void* X, const void* C, double* jones,
+                                const sc_lm_opts* opts, double* cost, int32_t* iters, int32_t prec, void* ws,
+                                size_t ws_bytes, void* stream) {
+  Ctx c;
+  int r = open_ctx(c, d, prec, ws, ws_bytes, stream);
+  if (r) return r;
+  if ((r = check_lm(opts))) return r;
+  if (!X || !C || !jones) return fail(SC_EINVAL, "X, C and jones must not be NULL");
+  if (prec == SC_MIXED) {
+    float* w = c.at<float>(c.L.w);
+    SC_LAUNCH(PK_OTHER, launch_w_from_C<float>(c.s, static_cast<const float*>(C), w, c.st));
+    r = lm_solve<float>(c, static_cast<const float*>(X), false, static_cast<const float*>(C), w, jones, *opts, cost,
+                        iters);
+  } else {
+    double* w = c.at<double>(c.L.w);
+    SC_LAUNCH(PK_OTHER, launch_w_from_C<double>(c.s, static_cast<const double*>(C), w, c.st));
+    r = lm_solve<double>(c, static_cast<const double*>(X), false, static_cast<const double*>(C), w, jones, *opts,
+                         cost, iters);
+  }
+  return r ? r : ok();
+}
+
+SC_API int32_t sc_calibrate_sage(const sc_dims* d, const double* uvw, const double* freqs, const sc_sky* sky,
+                                 const void* V, double* jones, const sc_sage_opts* opts, double* costs,
+                                 int32_t prec, void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  int r = open_ctx(c, d, prec, ws, ws_bytes, stream);
+  if (r) return r;
+  if ((r = check_sky(c.s, sky))) return r;
+  if (!opts) return fail(SC_EINVAL, "options are NULL");
+  if (opts->n_em < 0) return fail(SC_EINVAL, "n_em must be >= 0");
+  if ((r = check_lm(&opts->lm))) return r;
+  if (!uvw || !freqs || !V || !jones) return fail(SC_EINVAL, "uvw, freqs, V and jones must not be NULL");
+  r = prec == SC_MIXED
+          ? sage<float>(c, uvw, freqs, sky, static_cast<const float*>(V), jones, *opts, costs)
+          : sage<double>(c, uvw, freqs, sky, static_cast<const double*>(V), jones, *opts, costs);
+  return r ? r : ok();
+}
+
+}  // extern "C"

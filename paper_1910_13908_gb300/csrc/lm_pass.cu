@@ -1,0 +1,223 @@
+// Steps (b) and (c, gradient half): one streaming pass over the visibilities
+// of one cluster, and the per-station reduction that turns its per-baseline
+// sums into J^T r and the 2x2 blocks of J^T J.
+//
+// For baseline pq and coherency c = C_pq(t,f) the model is c J_p J_q^H.  The
+// pass forms, per visibility,
+//     X = Xin (+ c G_old)       (E-step data from the running residual)
+//     r = X - c G,   G = J_p J_q^H
+// and accumulates per baseline (over the timeslots of a chunk and all
+// channels) cost_b = sum |r|_F^2 and rho_b = sum conj(c) r.  The gradient of
+// the cost with respect to J_p is then -2 rho_b J_q and with respect to J_q
+// -2 rho_b^H J_p, so J^T r of station s is sum_o rho J_o (s = p) or
+// rho^H J_o (s = q).  The diagonal 8x8 block of J^T J of station s is the
+// real form of dJ_s -> dJ_s H_s with H_s = sum_o w_so J_o^H J_o, and
+// w_so = sum |c_so|^2 (see normal_eqs.cu).
+//
+// Memory: one thread per (baseline, timeslot chunk); consecutive threads take
+// consecutive baselines, whose [F][2][2] complex blocks are contiguous in the
+// [T][B][F][2][2] layout, so every warp streams contiguous memory.
+#include "sc_common.cuh"
+
+namespace sc {
+
+template <typename R, int FL>
+__global__ void __launch_bounds__(256) k_pass(int N, int T, int F, int64_t B, int nchunk, int tchunk,
+                                              const R* Xin, const R* __restrict__ C,
+                                              const double* __restrict__ J_old,
+                                              const double* __restrict__ J_cur, R* Rout,
+                                              R* __restrict__ stat_cost, R* __restrict__ stat_rho,
+                                              const LMState* __restrict__ lm) {
+  if (lm != nullptr && (lm->done | lm->skip)) return;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nchunk * B) return;
+  int chunk = (int)(idx / B);
+  int64_t b = idx - (int64_t)chunk * B;
+  int p, q;
+  bl_pair(b, N, p, q);
+  m22<R> G = mzero<R>(), Go = mzero<R>();
+  if (FL & P_SUB) G = mul_h(load_jones<R>(J_cur, p), load_jones<R>(J_cur, q));
+  if (FL & P_OLD) Go = mul_h(load_jones<R>(J_old, p), load_jones<R>(J_old, q));
+  R cost = 0;
+  m22<R> rho = mzero<R>();
+  int t0 = chunk * tchunk, t1 = min(T, t0 + tchunk);
+  for (int t = t0; t < t1; ++t) {
+    size_t v0 = ((size_t)t * B + b) * F;
+#pragma unroll 4
+    for (int f = 0; f < F; ++f) {
+      size_t v = v0 + f;
+      m22<R> x;
+      if (FL & P_WRITE_R) {
+        // may run in place (Rout == Xin): plain loads
+        const R* px = Xin + 8 * v;
+        x = {{px[0], px[1]}, {px[2], px[3]}, {px[4], px[5]}, {px[6], px[7]}};
+      } else {
+        x = ld_vis(Xin + 8 * v);
+      }
+      cx<R> c = ld_c(C + 2 * v);
+      if (FL & P_OLD) x = x + smul(c, Go);
+      if (FL & P_SUB) x = x - smul(c, G);
+      if (FL & P_WRITE_R) st_vis(Rout + 8 * v, x);
+      if (FL & P_STATS) {
+        cost += frob2(x);
+        rho.a = rho.a + cmulc(c, x.a);
+        rho.b = rho.b + cmulc(c, x.b);
+        rho.c = rho.c + cmulc(c, x.c);
+        rho.d = rho.d + cmulc(c, x.d);
+      }
+    }
+  }
+  if (FL & P_STATS) {
+    size_t o = (size_t)chunk * B + b;
+    stat_cost[o] = cost;
+    st_vis(stat_rho + 8 * o, rho);
+  }
+}
+
+template <typename R, int FL>
+static cudaError_t go_pass(const Shape& s, const R* Xin, const R* C, const double* J_old,
+                           const double* J_cur, R* Rout, R* stat_cost, R* stat_rho, int nchunk,
+                           int tchunk, const LMState* lm, cudaStream_t st) {
+  int64_t n = (int64_t)nchunk * s.B;
+  k_pass<R, FL><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s.N, s.T, s.F, s.B, nchunk, tchunk, Xin, C,
+                                                             J_old, J_cur, Rout, stat_cost, stat_rho, lm);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, const double* J_old,
+                        const double* J_cur, R* Rout, R* stat_cost, R* stat_rho, int nchunk,
+                        int tchunk, const LMState* lm, cudaStream_t st) {
+#define SC_PASS(FL) \
+  case FL:          \
+    return go_pass<R, FL>(s, Xin, C, J_old, J_cur, Rout, stat_cost, stat_rho, nchunk, tchunk, lm, st);
+  switch (flags) {
+    SC_PASS(P_OLD | P_SUB | P_STATS)              // LM pass on the running residual
+    SC_PASS(P_SUB | P_STATS)                      // LM pass on explicit data X
+    SC_PASS(P_STATS)                              // gradient sums of a given residual
+    SC_PASS(P_SUB | P_WRITE_R | P_STATS)          // residual + cost
+    SC_PASS(P_SUB | P_WRITE_R)                    // subtract one cluster's model
+    SC_PASS(P_OLD | P_SUB | P_WRITE_R)            // replace one cluster's model
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SC_PASS
+}
+template cudaError_t launch_pass<float>(const Shape&, int, const float*, const float*, const double*,
+                                        const double*, float*, float*, float*, int, int,
+                                        const LMState*, cudaStream_t);
+template cudaError_t launch_pass<double>(const Shape&, int, const double*, const double*, const double*,
+                                         const double*, double*, double*, double*, int, int,
+                                         const LMState*, cudaStream_t);
+
+// ---- per-station reduction ---------------------------------------------------------------
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_station_reduce(int N, int64_t B, int nchunk,
+                                                        const R* __restrict__ stat_cost,
+                                                        const R* __restrict__ stat_rho,
+                                                        const R* __restrict__ w,
+                                                        const double* __restrict__ J,
+                                                        double* __restrict__ g, double* __restrict__ H,
+                                                        double* __restrict__ cpart,
+                                                        const LMState* __restrict__ lm) {
+  if (lm != nullptr && (lm->done | lm->skip)) return;
+  __shared__ double sh[32];
+  int s = blockIdx.x;
+  double acc[13];
+#pragma unroll
+  for (int i = 0; i < 13; ++i) acc[i] = 0.0;
+  for (int o = threadIdx.x; o < N; o += blockDim.x) {
+    if (o == s) continue;
+    int64_t b = s < o ? bl_index(s, o, N) : bl_index(o, s, N);
+    m22<double> rho = mzero<double>();
+    double cst = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      size_t off = (size_t)c * B + b;
+      const R* pr = stat_rho + 8 * off;
+      rho.a.re += pr[0]; rho.a.im += pr[1]; rho.b.re += pr[2]; rho.b.im += pr[3];
+      rho.c.re += pr[4]; rho.c.im += pr[5]; rho.d.re += pr[6]; rho.d.im += pr[7];
+      cst += stat_cost[off];
+    }
+    m22<double> Jo = load_jones<double>(J, o);
+    m22<double> gam = s < o ? mul(rho, Jo) : mul(hconj(rho), Jo);
+    if (s < o) acc[12] += cst;
+    acc[0] += gam.a.re; acc[1] += gam.a.im; acc[2] += gam.b.re; acc[3] += gam.b.im;
+    acc[4] += gam.c.re; acc[5] += gam.c.im; acc[6] += gam.d.re; acc[7] += gam.d.im;
+    double wb = (double)w[b];
+    // w_so J_o^H J_o: (0,0), (1,1) real, (0,1) complex
+    acc[8] += wb * (norm2(Jo.a) + norm2(Jo.c));
+    acc[9] += wb * (norm2(Jo.b) + norm2(Jo.d));
+    cx<double> h01 = cmulc(Jo.a, Jo.b) + cmulc(Jo.c, Jo.d);
+    acc[10] += wb * h01.re;
+    acc[11] += wb * h01.im;
+  }
+  double tot[13];
+#pragma unroll
+  for (int i = 0; i < 13; ++i) tot[i] = block_sum(acc[i], sh);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 8; ++i) g[8 * s + i] = tot[i];
+    for (int i = 0; i < 4; ++i) H[4 * s + i] = tot[8 + i];
+    cpart[s] = tot[12];
+  }
+}
+
+template <typename R>
+cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
+                                  int nchunk, const R* w, const double* J, double* g, double* H,
+                                  double* cpart, const LMState* lm, cudaStream_t st) {
+  k_station_reduce<R><<<s.N, 256, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm);
+  return cudaGetLastError();
+}
+template cudaError_t launch_station_reduce<float>(const Shape&, const float*, const float*, int,
+                                                  const float*, const double*, double*, double*,
+                                                  double*, const LMState*, cudaStream_t);
+template cudaError_t launch_station_reduce<double>(const Shape&, const double*, const double*, int,
+                                                   const double*, const double*, double*, double*,
+                                                   double*, const LMState*, cudaStream_t);
+
+__global__ void k_sum_cost(const double* __restrict__ cpart, int N, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a += cpart[i];
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) *out = a;
+}
+
+cudaError_t launch_sum_cost(const double* cpart, int N, double* out, cudaStream_t st) {
+  k_sum_cost<<<1, 256, 0, st>>>(cpart, N, out);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_sum_reals(const R* __restrict__ x, int64_t n, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += (double)x[i];
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) *out = a;
+}
+
+template <typename R>
+cudaError_t launch_sum_reals(const R* x, int64_t n, double* out, cudaStream_t st) {
+  k_sum_reals<R><<<1, 1024, 0, st>>>(x, n, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_sum_reals<float>(const float*, int64_t, double*, cudaStream_t);
+template cudaError_t launch_sum_reals<double>(const double*, int64_t, double*, cudaStream_t);
+
+}  // namespace sc

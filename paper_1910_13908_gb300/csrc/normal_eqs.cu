@@ -1,0 +1,195 @@
+// Step (c): the Gauss-Newton matrix J^T J of one cluster, written densely
+// (8N x 8N) for the Cholesky factorisation, and the float64 product
+// (J^T J + mu D) x used by the iterative refinement of the float32 solve.
+//
+// With the unpolarised coherency c Id, a change dJ of the Jones changes the
+// model of baseline so by c (dJ_s J_o^H + J_s dJ_o^H), and J^T applied to
+// that change gives, for station s,
+//     (J^T J dJ)_s = dJ_s H_s + J_s sum_{o != s} w_so dJ_o^H J_o,
+//     H_s = sum_{o != s} w_so J_o^H J_o,   w_so = sum_{t,f} |c_so(t,f)|^2.
+// Written in the real parameters theta[8s + 4i + 2j + x] (x = 0 real,
+// 1 imaginary part of J_s[i][j]) the 8x8 blocks are
+//   off-diagonal (s, o), Z = w_so J_s[i][a] J_o[b][j], row (x,i,j), col (y,b,a):
+//       (0,0): Re Z   (1,0): Im Z   (0,1): Im Z   (1,1): -Re Z
+//   diagonal s, Hd = H_s + mu diag(H_s), row (x,i,j), col (y,i',a), i' = i:
+//       (0,0): Re Hd[a][j]   (1,0): Im Hd[a][j]   (0,1): -Im Hd[a][j]   (1,1): Re Hd[a][j]
+// (the real form of dJ_s -> dJ_s Hd and dJ_o -> w J_s dJ_o^H J_o).  The
+// matrix depends on the data only through w, so it is assembled in O(P^2)
+// without touching the visibilities; its cost is the matrix write itself.
+#include "sc_common.cuh"
+
+namespace sc {
+
+template <typename R>
+__device__ __forceinline__ cx<R> jent(const double* __restrict__ J, int s, int i, int j) {
+  const double* p = J + 8 * s + 4 * i + 2 * j;
+  return {(R)p[0], (R)p[1]};
+}
+
+__device__ __forceinline__ void st4(float* d, const float* v) {
+  *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* d, const double* v) {
+  reinterpret_cast<double2*>(d)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(d)[1] = make_double2(v[2], v[3]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_assemble(int N, int lda, int Ppad, const R* __restrict__ w,
+                                                  const double* __restrict__ J,
+                                                  const double* __restrict__ H,
+                                                  const LMState* __restrict__ lm, R* __restrict__ A,
+                                                  int damp, int full) {
+  if (lm != nullptr && lm->done) return;
+  int P = 8 * N;
+  int row = blockIdx.y;
+  int col0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (col0 >= Ppad) return;
+  if (!full && col0 > row) return;  // lower triangle (+ the 4-wide group on the diagonal)
+  R mu = (damp && lm != nullptr) ? (R)lm->mu : (R)0;
+  R out[4];
+  if (row >= P) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[u] = (col0 + u == row) ? (R)1 : (R)0;
+  } else {
+    int s = row >> 3, rr = row & 7;
+    int i = rr >> 2, j = (rr >> 1) & 1, x = rr & 1;
+    int o = col0 >> 3;
+    if (col0 >= P) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) out[u] = 0;
+    } else if (o != s) {
+      int64_t b = s < o ? bl_index(s, o, N) : bl_index(o, s, N);
+      R wb = w[b];
+      int bb = (col0 & 7) >> 2;  // row index b of J_o for these 4 columns
+      cx<R> Job = jent<R>(J, o, bb, j);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int cc = (col0 + u) & 3;
+        int a = cc >> 1, y = cc & 1;
+        cx<R> Z = jent<R>(J, s, i, a) * Job;
+        Z = scale(Z, wb);
+        R v;
+        if (x == 0 && y == 0) v = Z.re;
+        else if (x == 1 && y == 0) v = Z.im;
+        else if (x == 0 && y == 1) v = Z.im;
+        else v = -Z.re;
+        out[u] = v;
+      }
+    } else {
+      const double* h = H + 4 * s;
+      int ip = (col0 & 7) >> 2;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int cc = (col0 + u) & 3;
+        int a = cc >> 1, y = cc & 1;
+        R v = 0;
+        if (ip == i) {
+          cx<R> hd;
+          if (a == 0 && j == 0) hd = {(R)h[0] * ((R)1 + mu), (R)0};
+          else if (a == 1 && j == 1) hd = {(R)h[1] * ((R)1 + mu), (R)0};
+          else if (a == 0 && j == 1) hd = {(R)h[2], (R)h[3]};
+          else hd = {(R)h[2], -(R)h[3]};
+          if (x == 0 && y == 0) v = hd.re;
+          else if (x == 1 && y == 0) v = hd.im;
+          else if (x == 0 && y == 1) v = -hd.im;
+          else v = hd.re;
+        }
+        out[u] = v;
+      }
+    }
+  }
+  // lda and col0 are multiples of 4, so the 4 values are one aligned vector
+  R* dst = A + (size_t)row * lda + col0;
+  if (col0 < lda) st4(dst, out);
+}
+
+template <typename R>
+cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const double* J,
+                            const double* H, const LMState* lm, R* A, bool damp, bool full,
+                            cudaStream_t st) {
+  int groups = (Ppad + 3) / 4;
+  dim3 grd((groups + 127) / 128, Ppad);
+  k_assemble<R><<<grd, 128, 0, st>>>(s.N, lda, Ppad, w, J, H, lm, A, damp ? 1 : 0, full ? 1 : 0);
+  return cudaGetLastError();
+}
+template cudaError_t launch_assemble<float>(const Shape&, int, int, const float*, const double*,
+                                            const double*, const LMState*, float*, bool, bool,
+                                            cudaStream_t);
+template cudaError_t launch_assemble<double>(const Shape&, int, int, const double*, const double*,
+                                             const double*, const LMState*, double*, bool, bool,
+                                             cudaStream_t);
+
+// ---- float64 refinement residual r = g - (J^T J + mu D) x ---------------------------------
+
+__device__ __forceinline__ double bsum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[wi] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
+__device__ __forceinline__ m22<double> ld_m22(const double* p) {
+  return {{p[0], p[1]}, {p[2], p[3]}, {p[4], p[5]}, {p[6], p[7]}};
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_refine_residual(int N, const R* __restrict__ w,
+                                                         const double* __restrict__ J,
+                                                         const double* __restrict__ H,
+                                                         const double* __restrict__ g,
+                                                         const double* __restrict__ x,
+                                                         const LMState* __restrict__ lm,
+                                                         double* __restrict__ r) {
+  if (lm->done | lm->skip) return;
+  __shared__ double sh[32];
+  int s = blockIdx.x;
+  // K_s = sum_o w_so dJ_o^H J_o
+  m22<double> K = mzero<double>();
+  for (int o = threadIdx.x; o < N; o += blockDim.x) {
+    if (o == s) continue;
+    int64_t b = s < o ? bl_index(s, o, N) : bl_index(o, s, N);
+    double wb = (double)w[b];
+    m22<double> d = ld_m22(x + 8 * o);
+    m22<double> t = h_mul(d, load_jones<double>(J, o));
+    K.a = K.a + scale(t.a, wb); K.b = K.b + scale(t.b, wb);
+    K.c = K.c + scale(t.c, wb); K.d = K.d + scale(t.d, wb);
+  }
+  double k8[8] = {K.a.re, K.a.im, K.b.re, K.b.im, K.c.re, K.c.im, K.d.re, K.d.im};
+  double t8[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t8[i] = bsum(k8[i], sh);
+  if (threadIdx.x == 0) {
+    m22<double> Ks = {{t8[0], t8[1]}, {t8[2], t8[3]}, {t8[4], t8[5]}, {t8[6], t8[7]}};
+    const double* h = H + 4 * s;
+    double mu = lm->mu;
+    m22<double> Hd = {{h[0] * (1.0 + mu), 0.0}, {h[2], h[3]}, {h[2], -h[3]}, {h[1] * (1.0 + mu), 0.0}};
+    m22<double> ds = ld_m22(x + 8 * s);
+    m22<double> y = mul(ds, Hd) + mul(load_jones<double>(J, s), Ks);
+    double y8[8] = {y.a.re, y.a.im, y.b.re, y.b.im, y.c.re, y.c.im, y.d.re, y.d.im};
+    for (int i = 0; i < 8; ++i) r[8 * s + i] = g[8 * s + i] - y8[i];
+  }
+}
+
+template <typename R>
+cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, const double* H,
+                                   const double* g, const double* x, const LMState* lm,
+                                   double* r, cudaStream_t st) {
+  k_refine_residual<R><<<s.N, 256, 0, st>>>(s.N, w, J, H, g, x, lm, r);
+  return cudaGetLastError();
+}
+template cudaError_t launch_refine_residual<float>(const Shape&, const float*, const double*,
+                                                   const double*, const double*, const double*,
+                                                   const LMState*, double*, cudaStream_t);
+template cudaError_t launch_refine_residual<double>(const Shape&, const double*, const double*,
+                                                    const double*, const double*, const double*,
+                                                    const LMState*, double*, cudaStream_t);
+
+}  // namespace sc

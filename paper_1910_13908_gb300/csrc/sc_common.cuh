@@ -1,0 +1,278 @@
+// Shared device helpers: 2x2 complex algebra, baseline indexing, the device
+// LM state and the internal launcher declarations of every kernel file.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sagecal_gb.h"
+
+namespace sc {
+
+constexpr double kCLight = 299792458.0;
+constexpr int kNB = 64;          // Cholesky tile edge
+constexpr int kCholThreads = 256;
+
+// ---- complex scalars -----------------------------------------------------------
+
+template <typename R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R> __host__ __device__ __forceinline__ cx<R> cmk(R a, R b) { return {a, b}; }
+template <typename R> __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> __device__ __forceinline__ cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+template <typename R> __device__ __forceinline__ cx<R> scale(cx<R> a, R s) { return {a.re * s, a.im * s}; }
+// conj(a) * b
+template <typename R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename R> __device__ __forceinline__ R norm2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// ---- 2x2 complex matrices, row-major (a b; c d) ------------------------------------
+
+template <typename R>
+struct m22 {
+  cx<R> a, b, c, d;
+};
+
+template <typename R> __device__ __forceinline__ m22<R> operator+(const m22<R>& x, const m22<R>& y) {
+  return {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d};
+}
+template <typename R> __device__ __forceinline__ m22<R> operator-(const m22<R>& x, const m22<R>& y) {
+  return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d};
+}
+template <typename R> __device__ __forceinline__ m22<R> smul(cx<R> s, const m22<R>& x) {
+  return {s * x.a, s * x.b, s * x.c, s * x.d};
+}
+// x * y
+template <typename R> __device__ __forceinline__ m22<R> mul(const m22<R>& x, const m22<R>& y) {
+  return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+// x * y^H
+template <typename R> __device__ __forceinline__ m22<R> mul_h(const m22<R>& x, const m22<R>& y) {
+  return {x.a * conj(y.a) + x.b * conj(y.b), x.a * conj(y.c) + x.b * conj(y.d),
+          x.c * conj(y.a) + x.d * conj(y.b), x.c * conj(y.c) + x.d * conj(y.d)};
+}
+// x^H * y
+template <typename R> __device__ __forceinline__ m22<R> h_mul(const m22<R>& x, const m22<R>& y) {
+  return {cmulc(x.a, y.a) + cmulc(x.c, y.c), cmulc(x.a, y.b) + cmulc(x.c, y.d),
+          cmulc(x.b, y.a) + cmulc(x.d, y.c), cmulc(x.b, y.b) + cmulc(x.d, y.d)};
+}
+template <typename R> __device__ __forceinline__ m22<R> hconj(const m22<R>& x) {
+  return {conj(x.a), conj(x.c), conj(x.b), conj(x.d)};
+}
+template <typename R> __device__ __forceinline__ R frob2(const m22<R>& x) {
+  return norm2(x.a) + norm2(x.b) + norm2(x.c) + norm2(x.d);
+}
+template <typename R> __device__ __forceinline__ m22<R> mzero() {
+  return {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+}
+
+// Jones of station s from the float64 parameter vector (8 doubles).
+template <typename R>
+__device__ __forceinline__ m22<R> load_jones(const double* __restrict__ J, int s) {
+  const double2* p = reinterpret_cast<const double2*>(J + 8 * s);
+  double2 a = p[0], b = p[1], c = p[2], d = p[3];
+  return {{(R)a.x, (R)a.y}, {(R)b.x, (R)b.y}, {(R)c.x, (R)c.y}, {(R)d.x, (R)d.y}};
+}
+
+// ---- visibility element loads / stores (one 2x2 complex) ---------------------------
+
+__device__ __forceinline__ m22<float> ld_vis(const float* __restrict__ p) {
+  float4 u = __ldg(reinterpret_cast<const float4*>(p));
+  float4 v = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  return {{u.x, u.y}, {u.z, u.w}, {v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ m22<double> ld_vis(const double* __restrict__ p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  return {{a.x, a.y}, {b.x, b.y}, {c.x, c.y}, {d.x, d.y}};
+}
+__device__ __forceinline__ void st_vis(float* p, const m22<float>& x) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(x.a.re, x.a.im, x.b.re, x.b.im);
+  reinterpret_cast<float4*>(p)[1] = make_float4(x.c.re, x.c.im, x.d.re, x.d.im);
+}
+__device__ __forceinline__ void st_vis(double* p, const m22<double>& x) {
+  double2* q = reinterpret_cast<double2*>(p);
+  q[0] = make_double2(x.a.re, x.a.im);
+  q[1] = make_double2(x.b.re, x.b.im);
+  q[2] = make_double2(x.c.re, x.c.im);
+  q[3] = make_double2(x.d.re, x.d.im);
+}
+__device__ __forceinline__ cx<float> ld_c(const float* __restrict__ p) {
+  float2 u = __ldg(reinterpret_cast<const float2*>(p));
+  return {u.x, u.y};
+}
+__device__ __forceinline__ cx<double> ld_c(const double* __restrict__ p) {
+  double2 u = __ldg(reinterpret_cast<const double2*>(p));
+  return {u.x, u.y};
+}
+
+// ---- baselines -----------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ int64_t row_start(int p, int N) {
+  return (int64_t)p * N - (int64_t)p * (p + 1) / 2;
+}
+__host__ __device__ __forceinline__ int64_t bl_index(int p, int q, int N) {
+  return row_start(p, N) + (q - p - 1);
+}
+// inverse of bl_index
+__device__ __forceinline__ void bl_pair(int64_t b, int N, int& p, int& q) {
+  double n2 = 2.0 * N - 1.0;
+  int pp = (int)floor(0.5 * (n2 - sqrt(fmax(n2 * n2 - 8.0 * (double)b, 0.0))));
+  if (pp < 0) pp = 0;
+  if (pp > N - 2) pp = N - 2;
+  while (pp > 0 && row_start(pp, N) > b) --pp;
+  while (pp < N - 2 && row_start(pp + 1, N) <= b) ++pp;
+  p = pp;
+  q = (int)(b - row_start(pp, N)) + pp + 1;
+}
+
+// ---- device LM state ---------------------------------------------------------------
+
+struct LMState {
+  double mu, nu;
+  double cost, cost_trial, pred, rho;
+  double lm_tau, eps_grad;
+  int32_t iter, n_lm, done, notpd, skip, accepted;
+  int32_t pad[2];
+};
+
+// ---- workspace ------------------------------------------------------------------------
+
+// Offsets of every scratch buffer inside the caller's workspace.
+struct Workspace {
+  size_t total;
+  // always present
+  size_t status;     // uint32 device status word (+ padding)
+  size_t lm;         // LMState
+  // job-level buffers
+  size_t C;          // [K][T][B][F] complex  (SAGE only)
+  size_t w;          // [K][B] real
+  size_t wpart;      // [splits][B] real (predict partial sums)
+  size_t Rres;       // [T][B][F][4] complex running residual (SAGE only)
+  size_t E;          // [T][F][S_max][N] float2 station phasors (mixed)
+  size_t Sf;         // [F][S_max] float fluxes at each channel (mixed)
+  // per-solve buffers
+  size_t stat_cost;  // [nchunk][B] real
+  size_t stat_rho;   // [nchunk][B][8] real
+  size_t J_old, J_cur, J_trial;  // [8N] double
+  size_t g_cur, g_trial;         // [8N] double
+  size_t H_cur, H_trial;         // [4N] double
+  size_t cpart_cur, cpart_trial; // [N] double
+  size_t x, rvec, corr;          // [Ppad] double
+  size_t bvec;                   // [Ppad] real (rhs in the factor's precision)
+  size_t A;          // [Ppad][Ppad] real
+  size_t Linv;       // [nT][64][64] real
+  size_t sync;       // int: task counters, tile counters, flags
+  int nT, Ppad, nchunk, tchunk, splits;
+};
+
+struct Shape {
+  int N, T, F, K, S_max;
+  int64_t B;
+  int prec;  // SC_FP64 / SC_MIXED
+};
+
+// computes the layout; `job` = true to include the SAGE job buffers
+Workspace plan_workspace(const Shape& s, bool job);
+
+// ---- opt-in kernel timing (prof.cu) ---------------------------------------------------------
+
+enum ProfKind {
+  PK_PHASORS = 0,   // station phasors (mixed predict)
+  PK_COHERENCY,     // coherency contraction (mixed) / direct predict (FP64)
+  PK_PASS,          // streaming pass over the visibilities
+  PK_REDUCE,        // per-station reduction
+  PK_ASSEMBLE,      // J^T J assembly
+  PK_CHOL,          // Cholesky factorisation
+  PK_SOLVE,         // triangular solves
+  PK_REFINE,        // float64 refinement residual
+  PK_LM,            // LM control
+  PK_OTHER,         // small helpers (w sums, cost sums)
+  PK_COUNT
+};
+void prof_start(int kind, cudaStream_t st);
+void prof_stop(int kind, cudaStream_t st);  // also counts the launch
+unsigned long long launch_count();
+int prof_begin();
+int prof_end();
+void prof_read(int kind, long* n, double* ms);
+
+// ---- launchers (internal; all asynchronous on `st`) -------------------------------------
+
+// predict.cu
+cudaError_t launch_station_phasors(const Shape& s, const double* uvw, const double* freqs,
+                                   const double* l, const double* m, const double* flux,
+                                   const double* alpha, double f0, int S, float2* E, float* Sf,
+                                   cudaStream_t st);
+cudaError_t launch_coherency_f32(const Shape& s, int S, const float2* E, const float* Sf,
+                                 float2* C, float* wpart, int splits, cudaStream_t st);
+cudaError_t launch_predict_f64(const Shape& s, const double* uvw, const double* freqs,
+                               const double* l, const double* m, const double* flux,
+                               const double* alpha, double f0, int S, double2* C,
+                               cudaStream_t st);
+template <typename R>
+cudaError_t launch_w_from_C(const Shape& s, const R* C, R* w, cudaStream_t st);
+cudaError_t launch_sum_parts(const float* wpart, int splits, int64_t B, float* w, cudaStream_t st);
+
+// lm_pass.cu
+enum PassFlags { P_OLD = 1, P_SUB = 2, P_WRITE_R = 4, P_STATS = 8 };
+template <typename R>
+cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, const double* J_old,
+                        const double* J_cur, R* Rout, R* stat_cost, R* stat_rho, int nchunk,
+                        int tchunk, const LMState* lm, cudaStream_t st);
+template <typename R>
+cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
+                                  int nchunk, const R* w, const double* J, double* g, double* H,
+                                  double* cpart, const LMState* lm, cudaStream_t st);
+cudaError_t launch_sum_cost(const double* cpart, int N, double* out, cudaStream_t st);
+template <typename R>
+cudaError_t launch_sum_reals(const R* x, int64_t n, double* out, cudaStream_t st);
+
+// normal_eqs.cu
+template <typename R>
+cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const double* J,
+                            const double* H, const LMState* lm, R* A, bool damp, bool full,
+                            cudaStream_t st);
+template <typename R>
+cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, const double* H,
+                                   const double* g, const double* x, const LMState* lm,
+                                   double* r, cudaStream_t st);
+
+// cholesky.cu
+__host__ __device__ int4 chol_task(int nT, int t);   // (type, i, k, j), type -1 past the end
+__host__ __device__ int4 solve_task(int nT, int t);
+int chol_ntasks(int nT);
+int chol_sync_ints(int nT);
+template <typename R>
+cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
+                        cudaStream_t st);
+template <typename R>
+cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* sync,
+                              const double* b, R* bwork, double* x, int accumulate,
+                              uint32_t* status, const LMState* lm, cudaStream_t st);
+
+// lm_control.cu
+cudaError_t launch_lm_init(LMState* lm, const sc_lm_opts* o, int N, const double* H,
+                           const double* g, const double* cpart, const double* J_src,
+                           double* J_cur, cudaStream_t st);
+cudaError_t launch_lm_trial(LMState* lm, int N, int Ppad, const double* J_cur, const double* x,
+                            const double* H, const double* g, double* J_trial, cudaStream_t st);
+cudaError_t launch_lm_decide(LMState* lm, int N, const double* cpart_trial, double* J_cur,
+                             const double* J_trial, double* g_cur, const double* g_trial,
+                             double* H_cur, const double* H_trial, cudaStream_t st);
+cudaError_t launch_lm_finish(const LMState* lm, const double* J_cur, int N, double* J_out,
+                             double* cost_out, int32_t* iters_out, cudaStream_t st);
+
+}  // namespace sc

@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in include/sagecal_gb.h (ctypes).
+
+Argument marshalling only: every step of the calibration runs in the CUDA
+library libsagecal_gb.so.  Tensors are torch CUDA tensors (PyTorch provides
+device memory and streams); complex data are torch.complex64 (SC_MIXED) or
+torch.complex128 (SC_FP64) with the layouts of the header:
+
+    uvw    float64 [T][N][3]        freqs  float64 [F]
+    V, X, R  complex [T][B][F][2][2]
+    C      complex [K][T][B][F] (one cluster: [T][B][F])
+    jones  complex128 [K][N][2][2] (one cluster: [N][2][2])
+
+There is no fallback: if the library is missing or the device is not a
+CUDA device, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+from . import build as _build
+
+SC_FP64 = 0
+SC_MIXED = 1
+
+_c = ctypes
+_LIB = None
+
+
+class Dims(_c.Structure):
+    _fields_ = [("N", _c.c_int32), ("T", _c.c_int32), ("F", _c.c_int32),
+                ("K", _c.c_int32), ("S_max", _c.c_int32)]
+
+
+class SkyC(_c.Structure):
+    _fields_ = [("offsets", _c.POINTER(_c.c_int32)), ("l", _c.c_void_p), ("m", _c.c_void_p),
+                ("flux", _c.c_void_p), ("alpha", _c.c_void_p), ("f0", _c.c_double)]
+
+
+class LMOpts(_c.Structure):
+    _fields_ = [("n_lm", _c.c_int32), ("refine_sweeps", _c.c_int32),
+                ("tau", _c.c_double), ("eps_grad", _c.c_double)]
+
+
+class SageOpts(_c.Structure):
+    _fields_ = [("n_em", _c.c_int32), ("lm", LMOpts)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libsagecal_gb.so is not built (run __graft_entry__.build())")
+        L = _c.CDLL(path)
+        vp, i32, sz = _c.c_void_p, _c.c_int32, _c.c_size_t
+        D = _c.POINTER(Dims)
+        L.sc_version.restype = i32
+        L.sc_last_error.argtypes = [_c.c_char_p, sz]
+        L.sc_last_error.restype = i32
+        L.sc_workspace_size.argtypes = [D, i32, _c.POINTER(sz)]
+        L.sc_device_status.argtypes = [vp, sz, _c.POINTER(_c.c_uint32)]
+        L.sc_chol_schedule.argtypes = [i32, i32, _c.POINTER(i32), i32]
+        L.sc_predict_coherencies.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, i32, vp, sz, vp]
+        L.sc_residual.argtypes = [D, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+        L.sc_lm_normal_eqs.argtypes = [D, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+        L.sc_solve_cluster.argtypes = [D, vp, vp, vp, _c.POINTER(LMOpts), vp, vp, i32, vp, sz, vp]
+        L.sc_calibrate_sage.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, vp, _c.POINTER(SageOpts),
+                                        vp, i32, vp, sz, vp]
+        L.sc_launch_count.restype = _c.c_uint64
+        L.sc_profile_read.argtypes = [i32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_double)]
+        for f in ("sc_profile_begin", "sc_profile_end", "sc_profile_read"):
+            getattr(L, f).restype = i32
+        for f in ("sc_workspace_size", "sc_device_status", "sc_chol_schedule",
+                  "sc_predict_coherencies", "sc_residual", "sc_lm_normal_eqs",
+                  "sc_solve_cluster", "sc_calibrate_sage"):
+            getattr(L, f).restype = i32
+        _LIB = L
+    return _LIB
+
+
+class ScError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("sagecal_gb error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc):
+    if rc < 0:
+        buf = _c.create_string_buffer(512)
+        lib().sc_last_error(buf, 512)
+        raise ScError(rc, buf.value.decode(errors="replace"))
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else _c.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return _c.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _cdt(prec):
+    import torch
+    return torch.complex64 if prec == SC_MIXED else torch.complex128
+
+
+def _rdt(prec):
+    import torch
+    return torch.float32 if prec == SC_MIXED else torch.float64
+
+
+@dataclasses.dataclass
+class Shape:
+    N: int
+    T: int
+    F: int
+    K: int = 1
+    S_max: int = 0
+
+    @property
+    def B(self):
+        return self.N * (self.N - 1) // 2
+
+    def c(self):
+        return Dims(self.N, self.T, self.F, self.K, self.S_max)
+
+
+@dataclasses.dataclass
+class DeviceSky:
+    """Sky model on the device: SoA float64 tensors + host cluster offsets."""
+    l: object
+    m: object
+    flux: object
+    alpha: object
+    offsets: list
+    f0: float = 150e6
+
+    def c(self):
+        offs = (_c.c_int32 * len(self.offsets))(*[int(x) for x in self.offsets])
+        s = SkyC(offs, _ptr(self.l), _ptr(self.m), _ptr(self.flux), _ptr(self.alpha), float(self.f0))
+        s._keep = offs
+        return s
+
+    @property
+    def K(self):
+        return len(self.offsets) - 1
+
+    @property
+    def S_max(self):
+        return max([b - a for a, b in zip(self.offsets[:-1], self.offsets[1:])] + [0])
+
+    @staticmethod
+    def from_synth(sky, device="cuda"):
+        import torch
+        t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
+        return DeviceSky(t(sky.l), t(sky.m), t(sky.flux), t(sky.alpha),
+                         [int(x) for x in sky.offsets], float(sky.f0))
+
+
+def workspace_size(shape: Shape, prec: int) -> int:
+    n = _c.c_size_t(0)
+    d = shape.c()
+    _check(lib().sc_workspace_size(_c.byref(d), prec, _c.byref(n)))
+    return n.value
+
+
+def workspace(shape: Shape, prec: int, device="cuda"):
+    import torch
+    ws = torch.empty(workspace_size(shape, prec), dtype=torch.uint8, device=device)
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+def device_status(ws) -> int:
+    import torch
+    torch.cuda.synchronize(ws.device)
+    st = _c.c_uint32(0)
+    _check(lib().sc_device_status(_ptr(ws), ws.numel(), _c.byref(st)))
+    return st.value
+
+
+def chol_schedule(nT: int, which: int = 0):
+    n = _check(lib().sc_chol_schedule(nT, which, None, 0))
+    buf = (_c.c_int32 * (4 * n))()
+    _check(lib().sc_chol_schedule(nT, which, buf, n))
+    return [tuple(buf[4 * i:4 * i + 4]) for i in range(n)]
+
+
+PROFILE_KINDS = ["station_phasors", "coherency", "vis_pass", "station_reduce", "jhj_assemble",
+                 "cholesky", "tri_solve", "refine_residual", "lm_control", "other"]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().sc_launch_count())
+
+
+def profile_begin():
+    _check(lib().sc_profile_begin())
+
+
+def profile_end() -> dict:
+    """Stops per-kernel timing; returns {kind: (launches, total_ms)}."""
+    _check(lib().sc_profile_end())
+    out = {}
+    for k, name in enumerate(PROFILE_KINDS):
+        n, ms = _c.c_int64(0), _c.c_double(0)
+        _check(lib().sc_profile_read(k, _c.byref(n), _c.byref(ms)))
+        out[name] = (n.value, ms.value)
+    return out
+
+
+def _need(t, dtype, shape, name):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError("%s: expected contiguous CUDA %s %s, got %s %s" %
+                         (name, dtype, tuple(shape), t.dtype, tuple(t.shape)))
+
+
+def predict_coherencies(shape: Shape, uvw, freqs, sky: DeviceSky, prec: int, ws, out=None):
+    """C [K][T][B][F] of every cluster."""
+    import torch
+    K = sky.K
+    d = Shape(shape.N, shape.T, shape.F, K, max(shape.S_max, sky.S_max))
+    if out is None:
+        out = torch.empty((K, d.T, d.B, d.F), dtype=_cdt(prec), device=uvw.device)
+    _need(uvw, torch.float64, (d.T, d.N, 3), "uvw")
+    _need(freqs, torch.float64, (d.F,), "freqs")
+    _need(out, _cdt(prec), (K, d.T, d.B, d.F), "C")
+    dc, skc = d.c(), sky.c()
+    _check(lib().sc_predict_coherencies(_c.byref(dc), _ptr(uvw), _ptr(freqs), _c.byref(skc),
+                                        _ptr(out), prec, _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def residual(shape: Shape, X, C, jones, prec: int, ws, out=None, want_cost=True):
+    """R = X - J_p C J_q^H for one cluster, and cost = sum |R|^2 (device scalar)."""
+    import torch
+    d = Shape(shape.N, shape.T, shape.F, 1, shape.S_max)
+    _need(X, _cdt(prec), (d.T, d.B, d.F, 2, 2), "X")
+    _need(C, _cdt(prec), (d.T, d.B, d.F), "C")
+    _need(jones, torch.complex128, (d.N, 2, 2), "jones")
+    if out is None:
+        out = torch.empty_like(X)
+    cost = torch.zeros((), dtype=torch.float64, device=X.device) if want_cost else None
+    dc = d.c()
+    _check(lib().sc_residual(_c.byref(dc), _ptr(X), _ptr(C), _ptr(jones), _ptr(out), _ptr(cost),
+                             prec, _ptr(ws), ws.numel(), _stream()))
+    return out, cost
+
+
+def lm_normal_eqs(shape: Shape, R, C, jones, prec: int, ws):
+    """(J^T J [8N][8N], J^T r [8N]) of one cluster at residual R."""
+    import torch
+    d = Shape(shape.N, shape.T, shape.F, 1, shape.S_max)
+    _need(R, _cdt(prec), (d.T, d.B, d.F, 2, 2), "R")
+    _need(C, _cdt(prec), (d.T, d.B, d.F), "C")
+    _need(jones, torch.complex128, (d.N, 2, 2), "jones")
+    P = 8 * d.N
+    JhJ = torch.empty((P, P), dtype=_rdt(prec), device=R.device)
+    Jhr = torch.empty((P,), dtype=torch.float64, device=R.device)
+    dc = d.c()
+    _check(lib().sc_lm_normal_eqs(_c.byref(dc), _ptr(R), _ptr(C), _ptr(jones), _ptr(JhJ), _ptr(Jhr),
+                                  prec, _ptr(ws), ws.numel(), _stream()))
+    return JhJ, Jhr
+
+
+def lm_opts(n_lm=10, refine_sweeps=2, tau=1e-3, eps_grad=1e-12):
+    return LMOpts(int(n_lm), int(refine_sweeps), float(tau), float(eps_grad))
+
+
+def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_sweeps=2, tau=1e-3,
+                  eps_grad=1e-12):
+    """LM solve of one cluster; `jones` [N][2][2] complex128 is updated in place.
+    Returns (jones, cost, iters) with cost/iters device scalars."""
+    import torch
+    d = Shape(shape.N, shape.T, shape.F, 1, shape.S_max)
+    _need(X, _cdt(prec), (d.T, d.B, d.F, 2, 2), "X")
+    _need(C, _cdt(prec), (d.T, d.B, d.F), "C")
+    _need(jones, torch.complex128, (d.N, 2, 2), "jones")
+    cost = torch.zeros((), dtype=torch.float64, device=X.device)
+    iters = torch.zeros((), dtype=torch.int32, device=X.device)
+    o = lm_opts(n_lm, refine_sweeps, tau, eps_grad)
+    dc = d.c()
+    _check(lib().sc_solve_cluster(_c.byref(dc), _ptr(X), _ptr(C), _ptr(jones), _c.byref(o),
+                                  _ptr(cost), _ptr(iters), prec, _ptr(ws), ws.numel(), _stream()))
+    return jones, cost, iters
+
+
+def calibrate_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, ws, n_em=1,
+                   n_lm=10, refine_sweeps=2, tau=1e-3, eps_grad=1e-12, costs=None):
+    """The whole path for one job; `jones` [K][N][2][2] complex128 is updated in
+    place.  Returns (jones, costs [K] device float64)."""
+    import torch
+    K = sky.K
+    d = Shape(shape.N, shape.T, shape.F, K, max(shape.S_max, sky.S_max))
+    _need(uvw, torch.float64, (d.T, d.N, 3), "uvw")
+    _need(freqs, torch.float64, (d.F,), "freqs")
+    _need(V, _cdt(prec), (d.T, d.B, d.F, 2, 2), "V")
+    _need(jones, torch.complex128, (K, d.N, 2, 2), "jones")
+    if costs is None:
+        costs = torch.zeros((K,), dtype=torch.float64, device=V.device)
+    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad))
+    dc, skc = d.c(), sky.c()
+    _check(lib().sc_calibrate_sage(_c.byref(dc), _ptr(uvw), _ptr(freqs), _c.byref(skc), _ptr(V),
+                                   _ptr(jones), _c.byref(o), _ptr(costs), prec, _ptr(ws), ws.numel(),
+                                   _stream()))
+    return jones, costs
