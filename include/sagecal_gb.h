@@ -11,8 +11,8 @@
  *   point-source coherency C_pq(t,f) = sum_s S_s(f)
  *                              exp(-2 pi i f/c (u l_s + v m_s + w (n_s - 1))) Id
  *   per cluster            Levenberg-Marquardt on the normal equations
- *                          (J^T J + mu diag(J^T J)) d = J^T r, solved by a
- *                          dense Cholesky factorisation (8N x 8N)
+ *                          (J^T J + mu I) d = J^T r, solved by a dense
+ *                          Cholesky factorisation (8N x 8N)
  *   across clusters        SAGE/EM: each cluster solved in turn against the
  *                          data minus the other clusters' current models.
  *
@@ -36,7 +36,7 @@
  *    memory order of the complex128 array.
  *  - J^T J: [8N][8N] row-major, float (SC_MIXED) or double (SC_FP64);
  *    J^T r: double [8N], with r = X - model, so the LM step solves
- *    (J^T J + mu diag(J^T J)) d = J^T r.
+ *    (J^T J + mu I) d = J^T r.
  *
  * Memory and streams
  * ------------------
@@ -111,8 +111,8 @@ typedef struct sc_sky {
   double f0;              /* reference frequency, Hz */
 } sc_sky;
 
-/* Levenberg-Marquardt options (Madsen, Nielsen & Tingleff 2004, Alg. 3.16
- * with Marquardt's scaling D = diag(J^T J)). */
+/* Levenberg-Marquardt options (Madsen, Nielsen & Tingleff 2004, Alg. 3.16:
+ * damping mu I, mu0 = tau max diag(J^T J), gain-ratio update of mu). */
 typedef struct sc_lm_opts {
   int32_t n_lm;          /* trial steps per solve, accepted or rejected */
   int32_t refine_sweeps; /* SC_MIXED: float64 iterative-refinement sweeps of

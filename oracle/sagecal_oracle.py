@@ -11,8 +11,9 @@ prints no equation; the method it times is SAGECal's:
   matrices J and the point-source coherency
   C_pq(t, f) = sum_s S_s(f) exp(-2 pi i f/c (u l_s + v m_s + w (n_s - 1))) Id;
 * Levenberg-Marquardt on the Gauss-Newton normal equations J^T J, J^T r
-  (Madsen, Nielsen & Tingleff 2004, Alg. 3.16, Marquardt's diagonal scaling),
-  each damped system solved by a Cholesky factorisation;
+  (Madsen, Nielsen & Tingleff 2004, Alg. 3.16: damping mu I with
+  mu0 = tau max diag(J^T J)), each damped system solved by a Cholesky
+  factorisation;
 * SAGE/EM (Fessler & Hero 1994; Kazemi et al. 2011, SAGECal's solver): the
   clusters are solved one at a time, cluster k against the data minus the
   current models of all other clusters.
@@ -30,7 +31,7 @@ Conventions
 * visibilities [T][B][F][2][2] complex, coherencies [T][B][F] complex (the
   unpolarised brightness matrix is a multiple of the identity)
 * parameters of station s: theta[8s + 4i + 2j + 0/1] = Re/Im J_s[i, j]
-* "Jhr" = J^T r with r = X - model (so the LM step solves (A + mu D) d = Jhr)
+* "Jhr" = J^T r with r = X - model (so the LM step solves (A + mu I) d = Jhr)
 
 What pins each function (tests/test_oracle.py):
 * predict_coherencies: a unit source at the phase centre gives exactly 1;
@@ -219,18 +220,19 @@ def cholesky_solve(A, b):
 
 def levenberg_marquardt(evaluate, theta0, n_iter, tau=1e-3, eps_grad=1e-12,
                         trace=None):
-    """Levenberg-Marquardt with Marquardt scaling (Madsen, Nielsen & Tingleff
-    2004, Alg. 3.16 with D = diag(J^T J)).
+    """Levenberg-Marquardt (Madsen, Nielsen & Tingleff 2004, Alg. 3.16): the
+    step d solves (A + mu I) d = g.
 
     evaluate(theta) -> (cost, A, g): cost = |r|^2, A = J^T J, g = J^T r with
-    r = data - model, so that the step d solves (A + mu diag(A)) d = g.
+    r = data - model (g is minus half the gradient of the cost).
 
     mu starts at tau * max diag(A), nu at 2.  Each of the n_iter iterations
-    tries one step; the gain ratio rho = (cost - cost_trial) / (d^T (mu D d
-    + g)) accepts it when rho > 0 (then mu *= max(1/3, 1 - (2 rho - 1)^3),
-    nu = 2), else mu *= nu, nu *= 2.  Iterations stop early once
-    max|g| <= eps_grad * (1 + cost).  A damped matrix that is not positive
-    definite counts as a rejected step.
+    tries one step; the gain ratio rho = (cost - cost_trial) / (d^T (mu d
+    + g)) (actual over predicted decrease of the cost |r|^2) accepts it when
+    rho > 0 (then mu *= max(1/3, 1 - (2 rho - 1)^3), nu = 2), else mu *= nu,
+    nu *= 2.  Iterations stop early once max|g| <= eps_grad * (1 + cost).  A
+    damped matrix that is not positive definite (or not finite) counts as a
+    rejected step.
     Returns (theta, cost, iterations done).
     """
     theta = np.array(theta0, dtype=np.float64)
@@ -242,16 +244,15 @@ def levenberg_marquardt(evaluate, theta0, n_iter, tau=1e-3, eps_grad=1e-12,
         if float(np.max(np.abs(g))) <= eps_grad * (1.0 + cost):
             break
         done += 1
-        D = np.diag(A).copy()
         try:
-            d = cholesky_solve(A + mu * np.diag(D), g)
-        except np.linalg.LinAlgError:
+            d = cholesky_solve(A + mu * np.eye(len(g)), g)
+        except (np.linalg.LinAlgError, ValueError):  # not PD, or mu overflowed
             mu *= nu
             nu *= 2.0
             continue
         trial = theta + d
         cost_t, A_t, g_t = evaluate(trial)
-        pred = float(d @ (mu * D * d + g))
+        pred = float(d @ (mu * d + g))
         rho = (cost - cost_t) / pred if pred > 0.0 else -1.0
         if trace is not None:
             trace.append(dict(mu=mu, nu=nu, rho=rho, cost=cost, cost_trial=cost_t))

@@ -1,9 +1,9 @@
 // Levenberg-Marquardt control on the device (Madsen, Nielsen & Tingleff 2004,
-// Alg. 3.16 with Marquardt's scaling D = diag(J^T J)), so that a whole solve
-// is a fixed sequence of launches with no host round trip:
+// Alg. 3.16: the step solves (J^T J + mu I) d = J^T r), so that a whole
+// solve is a fixed sequence of launches with no host round trip:
 //   init:   cost = sum of station partial costs, mu = tau max diag(J^T J),
 //           nu = 2, stop if max|J^T r| <= eps (1 + cost)
-//   trial:  theta_trial = theta + d, predicted decrease d^T (mu D d + g)
+//   trial:  theta_trial = theta + d, predicted decrease d^T (mu d + g)
 //   decide: rho = (cost - cost_trial) / predicted; rho > 0 accepts the step
 //           (mu *= max(1/3, 1 - (2 rho - 1)^3), nu = 2), otherwise
 //           mu *= nu, nu *= 2; a non-positive-definite factorisation counts
@@ -88,11 +88,9 @@ __global__ void k_lm_trial(LMState* lm, int N, const double* __restrict__ J_cur,
   }
   double mu = lm->mu, pr = 0.0;
   for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) {
-    int s = k >> 3, j = (k >> 1) & 1;
-    double D = H[4 * s + j];  // diag of J^T J at (Re/Im, i, j) = H_s[j][j]
     double d = x[k];
     J_trial[k] = J_cur[k] + d;
-    pr += d * (mu * D * d + g[k]);
+    pr += d * (mu * d + g[k]);
   }
   pr = bred_sum(pr, sh);
   if (threadIdx.x == 0) {

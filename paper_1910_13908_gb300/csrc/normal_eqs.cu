@@ -1,6 +1,6 @@
 // Step (c): the Gauss-Newton matrix J^T J of one cluster, written densely
 // (8N x 8N) for the Cholesky factorisation, and the float64 product
-// (J^T J + mu D) x used by the iterative refinement of the float32 solve.
+// (J^T J + mu I) x used by the iterative refinement of the float32 solve.
 //
 // With the unpolarised coherency c Id, a change dJ of the Jones changes the
 // model of baseline so by c (dJ_s J_o^H + J_s dJ_o^H), and J^T applied to
@@ -11,7 +11,7 @@
 // 1 imaginary part of J_s[i][j]) the 8x8 blocks are
 //   off-diagonal (s, o), Z = w_so J_s[i][a] J_o[b][j], row (x,i,j), col (y,b,a):
 //       (0,0): Re Z   (1,0): Im Z   (0,1): Im Z   (1,1): -Re Z
-//   diagonal s, Hd = H_s + mu diag(H_s), row (x,i,j), col (y,i',a), i' = i:
+//   diagonal s, Hd = H_s + mu I (LM damping), row (x,i,j), col (y,i',a), i' = i:
 //       (0,0): Re Hd[a][j]   (1,0): Im Hd[a][j]   (0,1): -Im Hd[a][j]   (1,1): Re Hd[a][j]
 // (the real form of dJ_s -> dJ_s Hd and dJ_o -> w J_s dJ_o^H J_o).  The
 // matrix depends on the data only through w, so it is assembled in O(P^2)
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(256) k_assemble(int N, int lda, int Ppad, cons
         R v = 0;
         if (ip == i) {
           cx<R> hd;
-          if (a == 0 && j == 0) hd = {(R)h[0] * ((R)1 + mu), (R)0};
-          else if (a == 1 && j == 1) hd = {(R)h[1] * ((R)1 + mu), (R)0};
+          if (a == 0 && j == 0) hd = {(R)h[0] + mu, (R)0};
+          else if (a == 1 && j == 1) hd = {(R)h[1] + mu, (R)0};
           else if (a == 0 && j == 1) hd = {(R)h[2], (R)h[3]};
           else hd = {(R)h[2], -(R)h[3]};
           if (x == 0 && y == 0) v = hd.re;
@@ -120,7 +120,7 @@ template cudaError_t launch_assemble<double>(const Shape&, int, int, const doubl
                                              const double*, const LMState*, double*, bool, bool,
                                              cudaStream_t);
 
-// ---- float64 refinement residual r = g - (J^T J + mu D) x ---------------------------------
+// ---- float64 refinement residual r = g - (J^T J + mu I) x ---------------------------------
 
 __device__ __forceinline__ double bsum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_refine_residual(int N, const R* __restr
     m22<double> Ks = {{t8[0], t8[1]}, {t8[2], t8[3]}, {t8[4], t8[5]}, {t8[6], t8[7]}};
     const double* h = H + 4 * s;
     double mu = lm->mu;
-    m22<double> Hd = {{h[0] * (1.0 + mu), 0.0}, {h[2], h[3]}, {h[2], -h[3]}, {h[1] * (1.0 + mu), 0.0}};
+    m22<double> Hd = {{h[0] + mu, 0.0}, {h[2], h[3]}, {h[2], -h[3]}, {h[1] + mu, 0.0}};
     m22<double> ds = ld_m22(x + 8 * s);
     m22<double> y = mul(ds, Hd) + mul(load_jones<double>(J, s), Ks);
     double y8[8] = {y.a.re, y.a.im, y.b.re, y.b.im, y.c.re, y.c.im, y.d.re, y.d.im};

@@ -127,17 +127,24 @@ def test_normal_equations_match_oracle(prec, N):
 def test_solve_cluster_matches_oracle(prec, N):
     spec, uvw, f, sky, Jt, Cs, V = make_job(N=N, T=3, F=2, K=1, S=9, seed=5)
     J0 = np.tile(np.eye(2, dtype=complex), (spec.N, 1, 1))
-    J_ref, cost_ref, it_ref = O.lm_cluster(V, Cs[0], J0, 10)
     shp = sc.Shape(spec.N, spec.T, spec.F, 1, 9)
     ws = sc.workspace(shp, prec)
-    Jg = tdev(J0, torch.complex128)
-    _, cost, iters = sc.solve_cluster(shp, tdev(V, cdt(prec)), tdev(Cs[0], cdt(prec)), Jg, prec, ws,
-                                      n_lm=10, refine_sweeps=2)
-    Jn = Jg.cpu().numpy()
-    assert iters.item() == it_ref
-    assert abs(cost.item() - cost_ref) <= 1e-4 * cost_ref
-    assert O.aligned_error(Jn, J_ref) <= 1e-4
-    assert sc.device_status(ws) & 2 == 0
+    # the early gradient stop is an integer decided by rounding-level values
+    # near the minimum, so it is compared only as a bound; with the stop
+    # disabled both sides take exactly n_lm steps
+    for eps in (1e-12, 0.0):
+        J_ref, cost_ref, it_ref = O.lm_cluster(V, Cs[0], J0, 10, eps_grad=eps)
+        Jg = tdev(J0, torch.complex128)
+        _, cost, iters = sc.solve_cluster(shp, tdev(V, cdt(prec)), tdev(Cs[0], cdt(prec)), Jg, prec, ws,
+                                          n_lm=10, refine_sweeps=2, eps_grad=eps)
+        Jn = Jg.cpu().numpy()
+        if eps == 0.0:
+            assert iters.item() == it_ref == 10
+        else:
+            assert 1 <= iters.item() <= 10
+        assert abs(cost.item() - cost_ref) <= 1e-4 * cost_ref
+        assert O.aligned_error(Jn, J_ref) <= 1e-4
+        assert sc.device_status(ws) & 2 == 0
 
 
 # --- the whole path ---------------------------------------------------------------------------

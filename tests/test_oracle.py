@@ -186,10 +186,14 @@ def test_lm_on_a_linear_problem():
         return float(r @ r), M.T @ M, M.T @ r
 
     trace = []
-    th, cost, done = O.levenberg_marquardt(ev, np.zeros(5), 40, tau=1e-3, eps_grad=1e-14, trace=trace)
+    # heavy initial damping (tau = 10) keeps the first steps short, so the
+    # decrease of each is well above rounding
+    th, cost, done = O.levenberg_marquardt(ev, np.zeros(5), 200, tau=10.0, eps_grad=1e-14, trace=trace)
     ref = np.linalg.lstsq(M, y, rcond=None)[0]
-    np.testing.assert_allclose(th, ref, atol=1e-9)
-    mu0 = 1e-3 * np.max(np.diag(M.T @ M))
+    # the cost-based acceptance stalls once the remaining cost excess is below
+    # the rounding of the cost (|theta - ref| ~ 1e-8 here)
+    np.testing.assert_allclose(th, ref, atol=1e-7)
+    mu0 = 10.0 * np.max(np.diag(M.T @ M))
     assert trace[0]["mu"] == pytest.approx(mu0, rel=1e-15)
     for a, b in zip(trace[:3], trace[1:4]):
         assert a["rho"] == pytest.approx(1.0, abs=1e-6)
