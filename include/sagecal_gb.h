@@ -192,6 +192,34 @@ SC_API int32_t sc_residual(const sc_dims* d, const void* X, const void* C,
                            int32_t prec, void* ws, size_t ws_bytes,
                            void* stream);
 
+/* No-allocation variant of sc_residual, for callers that cannot allocate
+ * device memory and therefore cannot hand the library a workspace: for
+ * example a plug-in inside a host application whose own allocator already
+ * owns the whole GPU and offers no way to borrow from it, or a latency-bound
+ * loop that forbids cudaMalloc after start-up because an allocation can
+ * synchronise the device.  The paper has no counterpart to this call; it
+ * exists only for such callers.
+ *
+ * Same arguments, layouts and results as sc_residual, without the workspace
+ * (the cost is summed in a different order, so it agrees to rounding).  Its
+ * scratch is one 16 MiB array compiled into the library, which every GPU
+ * that loads the library holds until the process exits.  Rules:
+ *  - with cost != NULL the problem may have at most 466026 baselines
+ *    (N <= 965) in SC_MIXED and 233013 (N <= 683) in SC_FP64; larger ones
+ *    are rejected with SC_EINVAL before anything is launched;
+ *  - all calls on one device share the array, so calls that overlap on the
+ *    GPU (other streams, other host threads) race; serialise them;
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture;
+ *  - nothing needs clearing between calls: each call writes all the scratch
+ *    it then reads.
+ * The error message of this call goes to errbuf (may be NULL), not to
+ * sc_last_error(). */
+SC_API int32_t sc_residual_noalloc(const sc_dims* d, const void* X, const void* C,
+                                   const double* jones, void* R, double* cost,
+                                   int32_t prec, void* stream, char* errbuf,
+                                   size_t errlen);
+
 /* Step (c): Gauss-Newton normal equations of one cluster at residual R
  * (= X - model at `jones`):
  *   JhJ   DEVICE out [8N][8N] row-major, float (SC_MIXED) / double (SC_FP64),
