@@ -428,7 +428,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ska512", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--refine", type=int, default=2)
+    ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")

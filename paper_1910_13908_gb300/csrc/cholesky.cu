@@ -23,6 +23,7 @@
 // (ld.global.cg / st.global.cg), and published with a fence followed by a
 // release store of the tile's counter.
 #include <algorithm>
+#include <type_traits>
 
 #include "sc_common.cuh"
 
@@ -114,24 +115,50 @@ __device__ __forceinline__ uint32_t ld_status(const uint32_t* p) {
   return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
-// Waits until *p >= v.  Gives up (returns false) after kSpinLimit polls or as
-// soon as another CTA has recorded a timeout.
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Waits until *p >= v.  Polls with relaxed loads (an acquire load on every
+// poll would invalidate this SM's L1 each time and stall the load/store
+// path of the other CTAs sharing the SM) and takes one acquire fence once
+// the counter is seen.  Gives up (returns false) after kSpinLimit polls or
+// as soon as another CTA has recorded a timeout.
 __device__ bool wait_ge(const int* p, int v, uint32_t* status) {
+#ifdef SC_SPIN_ACQUIRE
   for (long it = 0; it < kSpinLimit; ++it) {
     if (ld_acquire(p) >= v) return true;
     if ((it & 63) == 63 && (ld_status(status) & SC_STATUS_TIMEOUT)) return false;
     __nanosleep(it < 16 ? 32 : 200);
   }
+#else
+  for (long it = 0; it < kSpinLimit; ++it) {
+    if (ld_relaxed(p) >= v) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      return true;
+    }
+    if ((it & 63) == 63 && (ld_status(status) & SC_STATUS_TIMEOUT)) return false;
+    __nanosleep(it < 16 ? 32 : 200);
+  }
+#endif
   atomicOr(status, SC_STATUS_TIMEOUT);
   return false;
 }
 
 // ---- tile helpers --------------------------------------------------------------------------
 
-constexpr int LD = kNB + 1;  // padded shared-memory row
+// Shared-memory row pitch: 64 elements + 16 bytes, so that rows stay 16-byte
+// aligned for vector loads and consecutive rows start 4 banks apart.
+template <typename R>
+struct Pitch {
+  static constexpr int value = kNB + 16 / (int)sizeof(R);
+};
 
 template <typename R>
 __device__ __forceinline__ void load_tile(R* sm, const R* g, int lda) {
+  constexpr int LD = Pitch<R>::value;
   for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
     sm[r * LD + c] = __ldcg(g + (size_t)r * lda + c);
@@ -139,115 +166,346 @@ __device__ __forceinline__ void load_tile(R* sm, const R* g, int lda) {
 }
 template <typename R>
 __device__ __forceinline__ void store_tile(R* g, int lda, const R* sm) {
+  constexpr int LD = Pitch<R>::value;
   for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
     int r = e >> 6, c = e & 63;
     __stcg(g + (size_t)r * lda + c, sm[r * LD + c]);
   }
 }
 
-// acc[a][b] = sum_m X[ty+16a][m] Y[tx+16b][m]   (X Y^T on 64x64 tiles)
-template <typename R>
-__device__ __forceinline__ void gemm_nt(R acc[4][4], const R* X, const R* Y) {
+// acc[a][b] = sum_m X[ty+16a][m] Y[tx+16b][m]   (X Y^T on 64x64 tiles); the
+// contraction index is contiguous in both operands, so each thread reads
+// 16-byte vectors along it.
+__device__ __forceinline__ void gemm_nt(float acc[4][4], const float* X, const float* Y) {
+  constexpr int L = Pitch<float>::value;
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-#pragma unroll 4
-  for (int m = 0; m < kNB; ++m) {
-    R x[4], y[4];
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
+  for (int m = 0; m < kNB; m += 4) {
+    float4 x[4], y[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) x[a] = X[(ty + 16 * a) * LD + m];
+    for (int a = 0; a < 4; ++a) x[a] = *reinterpret_cast<const float4*>(X + (ty + 16 * a) * L + m);
 #pragma unroll
-    for (int b = 0; b < 4; ++b) y[b] = Y[(tx + 16 * b) * LD + m];
+    for (int b = 0; b < 4; ++b) y[b] = *reinterpret_cast<const float4*>(Y + (tx + 16 * b) * L + m);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+      for (int b = 0; b < 4; ++b) {
+        float t = acc[a][b];
+        t = fmaf(x[a].x, y[b].x, t);
+        t = fmaf(x[a].y, y[b].y, t);
+        t = fmaf(x[a].z, y[b].z, t);
+        t = fmaf(x[a].w, y[b].w, t);
+        acc[a][b] = t;
+      }
+  }
+}
+__device__ __forceinline__ void gemm_nt(double acc[4][4], const double* X, const double* Y) {
+  constexpr int L = Pitch<double>::value;
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+#pragma unroll 2
+  for (int m = 0; m < kNB; m += 2) {
+    double2 x[4], y[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) x[a] = *reinterpret_cast<const double2*>(X + (ty + 16 * a) * L + m);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) y[b] = *reinterpret_cast<const double2*>(Y + (tx + 16 * b) * L + m);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(x[a].y, y[b].y, fma(x[a].x, y[b].x, acc[a][b]));
   }
 }
 
-// In-place Cholesky of the 64x64 tile in sm (lower part read), writing L
-// (upper part zeroed); then Linv = L^-1 into sv.  Non-positive pivots are
-// replaced by 1 and reported through *bad.
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
+// Compile-time loops: every step below is instantiated with constant
+// indices, so the per-lane rows stay in registers.
+template <int I, int N>
+struct Static {
+  template <typename F>
+  __device__ __forceinline__ static void each(F&& f) {
+    f(std::integral_constant<int, I>());
+    Static<I + 1, N>::each(f);
+  }
+};
+template <int N>
+struct Static<N, N> {
+  template <typename F>
+  __device__ __forceinline__ static void each(F&&) {}
+};
+
+// Cholesky of a 32x32 SPD block held by one warp, row i in lane i
+// (a[j] = A[i][j], j <= i read).  Pivots and column values move by
+// shuffles, no barrier.  On return a[j] = L[i][j] for j <= i and 0 above.
+// A non-positive pivot is replaced by 1 and sets *bad.
 template <typename R>
-__device__ void potrf_tile(R* sm, R* sv, R* piv, int* bad) {
-  int tid = threadIdx.x;
-  int r = tid >> 2, cb = tid & 3;
-  for (int c = 0; c < kNB; ++c) {
-    R p = sm[c * LD + c];
+__device__ __forceinline__ void warp_potrf32(R (&a)[32], int lane, int* bad) {
+  Static<0, 32>::each([&](auto cc) {
+    constexpr int c = decltype(cc)::value;
+    R p = __shfl_sync(0xffffffffu, a[c], c);
     if (!(p > (R)0)) {
       p = (R)1;
-      if (tid == 0) *bad = 1;
+      if (lane == 0) *bad = 1;
     }
-    if (tid == 0) piv[c] = p;
-    if (r > c) {
-      R arc = sm[r * LD + c] / p;
+    R rs = rsqrt(p);
+    R lic = (lane == c) ? p * rs : a[c] * rs;  // L[i][c] (meaningful for i >= c)
+    a[c] = lic;
+    Static<c + 1, 32>::each([&](auto jj) {
+      constexpr int j = decltype(jj)::value;
+      R ljc = __shfl_sync(0xffffffffu, lic, j);
+      if (lane >= j) a[j] -= lic * ljc;
+    });
+  });
+  Static<0, 32>::each([&](auto jj) {
+    constexpr int j = decltype(jj)::value;
+    if (j > lane) a[j] = 0;
+  });
+}
+
+// Inverse of a 32x32 lower-triangular L held one row per lane (l[j] =
+// L[i][j]); returns x[j] = (L^-1)[i][j].  Row operations on the identity:
+// after step m row m of the inverse is final and is broadcast by shuffles.
+template <typename R>
+__device__ __forceinline__ void warp_trinv32(const R (&l)[32], R (&x)[32], int lane) {
+  Static<0, 32>::each([&](auto jj) {
+    constexpr int j = decltype(jj)::value;
+    x[j] = (j == lane) ? (R)1 : (R)0;
+  });
+  Static<0, 32>::each([&](auto mm) {
+    constexpr int m = decltype(mm)::value;
+    R dinv = rcp_rn(__shfl_sync(0xffffffffu, l[m], m));
+    if (lane == m) {
+      Static<0, m + 1>::each([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        x[k] *= dinv;
+      });
+    }
+    R lrm = l[m];  // L[lane][m]
+    Static<0, m + 1>::each([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      R xmk = __shfl_sync(0xffffffffu, x[k], m);
+      if (lane > m) x[k] -= lrm * xmk;
+    });
+  });
+}
+
+// One warp: Cholesky and inverse of the 32x32 block at Ablk (pitch ld, lower
+// part read), writing L to Ablk and L^-1 to Xblk.  Kept out of line so that
+// the two calls of a tile factorisation share one copy of the fully
+// unrolled code (it runs once per panel, straight from the instruction
+// cache rather than L2).
+template <typename R>
+__device__ __noinline__ void warp_block32(R* Ablk, R* Xblk, int ld, int lane, int* bad) {
+  R a[32], x[32];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        int cc = cb + 4 * u;
-        if (cc > c && cc <= r) sm[r * LD + cc] -= arc * sm[cc * LD + c];
-      }
-    }
-    __syncthreads();
+  for (int j = 0; j < 32; ++j) a[j] = Ablk[lane * ld + j];
+  warp_potrf32(a, lane, bad);
+  warp_trinv32(a, x, lane);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    Ablk[lane * ld + j] = a[j];
+    Xblk[lane * ld + j] = x[j];
+  }
+}
+
+// C[r][c] (+)= sign * sum_m X[r][m] Y[c][m] on 32x32 blocks in shared memory
+// (pitch ld), 256 threads, 2x2 outputs each.
+template <typename R>
+__device__ __forceinline__ void gemm32_nt(R* C, const R* X, const R* Y, int ld, R sign, bool accumulate) {
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  R acc[2][2] = {{0, 0}, {0, 0}};
+#pragma unroll 8
+  for (int m = 0; m < 32; ++m) {
+    R x0 = X[ty * ld + m], x1 = X[(ty + 16) * ld + m];
+    R y0 = Y[tx * ld + m], y1 = Y[(tx + 16) * ld + m];
+    acc[0][0] = fma(x0, y0, acc[0][0]);
+    acc[0][1] = fma(x0, y1, acc[0][1]);
+    acc[1][0] = fma(x1, y0, acc[1][0]);
+    acc[1][1] = fma(x1, y1, acc[1][1]);
   }
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    int cc = cb + 4 * u;
-    R v;
-    if (cc < r) v = sm[r * LD + cc] / sqrt(piv[cc]);
-    else if (cc == r) v = sqrt(piv[r]);
-    else v = 0;
-    sm[r * LD + cc] = v;
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      R* p = C + (ty + 16 * a) * ld + tx + 16 * b;
+      *p = accumulate ? *p + sign * acc[a][b] : sign * acc[a][b];
+    }
+}
+
+// In-place Cholesky of the 64x64 tile in sm (lower part read), writing L
+// (upper part zeroed) back to sm and Linv = L^-1 to sv, from 32x32 blocks:
+//   L11 = chol(A11), Linv11          warp 0, registers + shuffles
+//   L21 = A21 Linv11^T              whole CTA
+//   A22 -= L21 L21^T                whole CTA
+//   L22 = chol(A22), Linv22          warp 0
+//   Linv21 = -Linv22 (L21 Linv11)    whole CTA (via the scratch block W)
+// aux holds a 32x32 scratch block (pitch of the tile).
+template <typename R>
+__device__ void potrf_tile(R* sm, R* sv, R* aux, int* bad) {
+  constexpr int LD = Pitch<R>::value;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  R* A11 = sm;
+  R* A21 = sm + 32 * LD;
+  R* A22 = sm + 32 * LD + 32;
+  R* X11 = sv;
+  R* X21 = sv + 32 * LD;
+  R* X22 = sv + 32 * LD + 32;
+  R* W = aux;  // 32 x LD scratch
+  if (warp == 0) {
+    warp_block32(A11, X11, LD, lane, bad);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      sm[lane * LD + 32 + j] = 0;   // upper-right block of L
+      sv[lane * LD + 32 + j] = 0;   // upper-right block of Linv
+    }
   }
   __syncthreads();
-  // Linv: column c = tid/4 by forward substitution, 4 lanes per column
-  int c = tid >> 2, part = tid & 3;
-  for (int rr = 0; rr < kNB; ++rr) {
-    R s = 0;
-    if (rr > c)
-      for (int m = c + part; m < rr; m += 4) s += sm[rr * LD + m] * sv[m * LD + c];
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (part == 0) {
-      R v = 0;
-      if (rr == c) v = (R)1 / sm[rr * LD + rr];
-      else if (rr > c) v = -s / sm[rr * LD + rr];
-      sv[rr * LD + c] = v;
-    }
-    __syncwarp();
+  gemm32_nt(W, A21, X11, LD, (R)1, false);        // W = L21 = A21 Linv11^T
+  __syncthreads();
+  for (int e = tid; e < 32 * 32; e += blockDim.x) A21[(e >> 5) * LD + (e & 31)] = W[(e >> 5) * LD + (e & 31)];
+  __syncthreads();
+  gemm32_nt(A22, A21, A21, LD, (R)-1, true);      // A22 -= L21 L21^T
+  __syncthreads();
+  if (warp == 0) warp_block32(A22, X22, LD, lane, bad);
+  // W <- L21 Linv11 (note: X11 is lower; W[r][c] = sum_m L21[r][m] X11[m][c])
+  // computed as  sum_m L21[r][m] X11t[c][m]  with X11t = X11^T staged in X21
+  for (int e = tid; e < 32 * 32; e += blockDim.x) {
+    int r = e >> 5, c = e & 31;
+    X21[c * LD + r] = X11[r * LD + c];
   }
+  __syncthreads();
+  gemm32_nt(W, A21, X21, LD, (R)1, false);        // W = L21 Linv11
+  __syncthreads();
+  // X21 <- -Linv22 W : sum_m X22[r][m] W[m][c]; stage W^T in X21 first
+  for (int e = tid; e < 32 * 32; e += blockDim.x) {
+    int r = e >> 5, c = e & 31;
+    X21[c * LD + r] = W[r * LD + c];
+  }
+  __syncthreads();
+  gemm32_nt(W, X22, X21, LD, (R)-1, false);       // W = -Linv22 (L21 Linv11)
+  __syncthreads();
+  for (int e = tid; e < 32 * 32; e += blockDim.x) X21[(e >> 5) * LD + (e & 31)] = W[(e >> 5) * LD + (e & 31)];
   __syncthreads();
 }
 
 // ---- factorisation ---------------------------------------------------------------------------
+
+// Tasks of the diagonal chain, run by one CTA (the "walker") without flag
+// round trips: POTRF(j), TRSM(j+1, j), UPDATE(j+1, j+1, j) for every j.
+__device__ __forceinline__ bool walker_task(int4 tk) {
+  return tk.x == T_POTRF || (tk.x == T_TRSM && tk.y == tk.w + 1) ||
+         (tk.x == T_UPD && tk.y == tk.w + 1 && tk.z == tk.w + 1);
+}
+
+// The walker: keeps the diagonal tile, its inverse and the next panel tile
+// in shared memory and walks the critical path of the factorisation,
+// publishing each result for the other CTAs.  Its own tasks appear in the
+// list in the order it runs them, and it waits only on earlier tasks, so the
+// list-order argument against deadlock still holds.
+template <typename R>
+__device__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32_t* status, LMState* lm,
+                            R* T0, R* T1, R* T2, R* aux, int* s_bad, int* s_ok) {
+  constexpr int LD = Pitch<R>::value;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  load_tile(T0, A, lda);
+  for (int j = 0; j < nT; ++j) {
+    if (threadIdx.x == 0) *s_bad = 0;
+    __syncthreads();
+    R* Ajj = A + (size_t)j * kNB * lda + (size_t)j * kNB;
+    potrf_tile(T0, T1, aux, s_bad);                 // T0 = L_jj, T1 = Linv_jj
+    store_tile(Ajj, lda, T0);
+    store_tile(Linv + (size_t)j * kNB * kNB, kNB, T1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (*s_bad) {
+        atomicOr(status, SC_STATUS_NOTPD);
+        if (lm != nullptr) lm->notpd = 1;
+      }
+      __threadfence();
+      st_release(sv.pdone + j, 1);
+    }
+    if (j + 1 == nT) break;
+    // TRSM(j+1, j): L_{j+1,j} = A_{j+1,j} Linv_jj^T, kept in T2
+    R* Ap = A + (size_t)(j + 1) * kNB * lda + (size_t)j * kNB;
+    if (threadIdx.x == 0) *s_ok = wait_ge(sv.upd + (j + 1) * nT + j, j, status);
+    __syncthreads();
+    if (!*s_ok) {
+      if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
+      return;
+    }
+    load_tile(T2, Ap, lda);
+    __syncthreads();
+    R acc[4][4];
+    gemm_nt(acc, T2, T1);
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int r = ty + 16 * a, c = tx + 16 * b;
+        T2[r * LD + c] = acc[a][b];
+        __stcg(Ap + (size_t)r * lda + c, acc[a][b]);
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(sv.tdone + (j + 1) * nT + j, 1);
+    }
+    // UPDATE(j+1, j+1, j): the next diagonal tile, kept in T0 for POTRF(j+1)
+    if (threadIdx.x == 0) *s_ok = wait_ge(sv.upd + (j + 1) * nT + (j + 1), j, status);
+    __syncthreads();
+    if (!*s_ok) {
+      if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
+      return;
+    }
+    load_tile(T0, A + (size_t)(j + 1) * kNB * lda + (size_t)(j + 1) * kNB, lda);
+    __syncthreads();
+    gemm_nt(acc, T2, T2);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) T0[(ty + 16 * a) * LD + tx + 16 * b] -= acc[a][b];
+  }
+}
 
 template <typename R>
 __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int lda, int nT,
                                                       R* __restrict__ Linv, int n_tasks,
                                                       int* sync, uint32_t* status, LMState* lm) {
   if (lm != nullptr && lm->done) return;
+  constexpr int LD = Pitch<R>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* s0 = reinterpret_cast<R*>(smraw);
   R* s1 = s0 + kNB * LD;
-  R* piv = s1 + kNB * LD;
+  R* s2 = s1 + kNB * LD;
+  R* aux = s2 + kNB * LD;
   __shared__ int s_task, s_ok, s_bad;
   SyncView sv(sync, nT);
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_task = atomicAdd(sv.fctr, 1);
-      s_bad = 0;
-    }
+    __syncthreads();  // every thread has read the previous s_task
+    if (threadIdx.x == 0) s_task = atomicAdd(sv.fctr, 1);
     __syncthreads();
     int t = s_task;
     if (t >= n_tasks) break;
+    if (t == 0) {
+      chol_walker(A, lda, nT, Linv, sv, status, lm, s0, s1, s2, aux, &s_bad, &s_ok);
+      break;
+    }
     int4 tk = chol_task(nT, t);
+    if (walker_task(tk)) continue;
     int i = tk.y, k = tk.z, j = tk.w;
     if (threadIdx.x == 0) {
-      bool ok = true;
-      if (tk.x == T_POTRF) {
-        ok = wait_ge(sv.upd + j * nT + j, j, status);
-      } else if (tk.x == T_TRSM) {
+      bool ok;
+      if (tk.x == T_TRSM) {
         ok = wait_ge(sv.pdone + j, 1, status) && wait_ge(sv.upd + i * nT + j, j, status);
       } else {
         ok = wait_ge(sv.tdone + i * nT + j, 1, status) && wait_ge(sv.tdone + k * nT + j, 1, status) &&
@@ -260,30 +518,14 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
       if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
       break;
     }
-    if (tk.x == T_POTRF) {
-      R* Ajj = A + (size_t)j * kNB * lda + (size_t)j * kNB;
-      load_tile(s0, Ajj, lda);
-      __syncthreads();
-      potrf_tile(s0, s1, piv, &s_bad);
-      store_tile(Ajj, lda, s0);
-      store_tile(Linv + (size_t)j * kNB * kNB, kNB, s1);  // Linv tiles: leading dim 64
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        if (s_bad) {
-          atomicOr(status, SC_STATUS_NOTPD);
-          if (lm != nullptr) lm->notpd = 1;
-        }
-        __threadfence();
-        st_release(sv.pdone + j, 1);
-      }
-    } else if (tk.x == T_TRSM) {
+    int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    R acc[4][4];
+    if (tk.x == T_TRSM) {
       R* Aij = A + (size_t)i * kNB * lda + (size_t)j * kNB;
       load_tile(s0, Aij, lda);
       load_tile(s1, Linv + (size_t)j * kNB * kNB, kNB);
       __syncthreads();
-      R acc[4][4];
       gemm_nt(acc, s0, s1);
-      int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -300,9 +542,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
       load_tile(s0, Lij, lda);
       load_tile(s1, Lkj, lda);
       __syncthreads();
-      R acc[4][4];
       gemm_nt(acc, s0, s1);
-      int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -338,7 +578,7 @@ template <typename R>
 cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
                         cudaStream_t st) {
   int n_tasks = chol_ntasks(nT);
-  size_t smem = sizeof(R) * (2 * kNB * LD + kNB);
+  size_t smem = sizeof(R) * (3 * kNB + 32) * Pitch<R>::value;
   const void* fn = reinterpret_cast<const void*>(&k_chol<R>);
   int grid = std::min(chol_grid<R>(fn, smem), n_tasks);
   cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * chol_factor_reset_ints(nT), st);
@@ -353,10 +593,29 @@ template cudaError_t launch_chol<double>(double*, int, int, double*, int*, uint3
 
 // ---- triangular solves ------------------------------------------------------------------------
 
+// Asynchronous copy of one 64x64 tile into shared memory (16-byte cp.async,
+// L2 only), as one commit group.
+template <typename R>
+__device__ __forceinline__ void tile_async(R* sm, const R* g, int lda) {
+  constexpr int LD = Pitch<R>::value;
+  constexpr int PER_ROW = kNB * (int)sizeof(R) / 16;
+  for (int e = threadIdx.x; e < kNB * PER_ROW; e += blockDim.x) {
+    int r = e / PER_ROW, ch = e - r * PER_ROW;
+    const char* src = reinterpret_cast<const char*>(g + (size_t)r * lda) + 16 * ch;
+    unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char*>(sm + r * LD) + 16 * ch);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void async_commit_empty() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // out[r] = sum_m T[r][m] v[m] (trans = 0) or sum_m T[m][r] v[m] (trans = 1) for a
 // 64x64 tile in shared memory; 4 threads per r, combined through red[4][64].
 template <typename R>
 __device__ __forceinline__ R tile_matvec(const R* Tm, const R* v, R* red, int trans) {
+  constexpr int LD = Pitch<R>::value;
   int r = threadIdx.x & 63, part = threadIdx.x >> 6;
   R s = 0;
 #pragma unroll 4
@@ -369,6 +628,10 @@ __device__ __forceinline__ R tile_matvec(const R* Tm, const R* v, R* red, int tr
   return tot;
 }
 
+// Block substitution, one task per tile row: FWD(i) y_i = Linv_ii (b_i -
+// sum_{j<i} L_ij y_j), BWD(i) x_i = Linv_ii^T (y_i - sum_{j>i} L_ji^T x_j).
+// A task streams its tiles through two shared buffers: the copy of the next
+// tile is in flight while it waits for the current dependency.
 template <typename R>
 __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict__ A, int lda, int nT,
                                                             const R* __restrict__ Linv,
@@ -378,22 +641,34 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
                                                             int accumulate, uint32_t* status,
                                                             const LMState* lm) {
   if (lm != nullptr && (lm->done | lm->notpd)) return;
+  constexpr int LD = Pitch<R>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
-  R* tile = reinterpret_cast<R*>(smraw);
-  R* vin = tile + kNB * LD;
+  R* buf0 = reinterpret_cast<R*>(smraw);
+  R* buf1 = buf0 + kNB * LD;
+  R* vin = buf1 + kNB * LD;
   R* red = vin + kNB;
   __shared__ int s_task, s_ok;
   SyncView sv(sync, nT);
   int r = threadIdx.x & 63, part = threadIdx.x >> 6;
   for (;;) {
+    __syncthreads();
     if (threadIdx.x == 0) s_task = atomicAdd(sv.sctr, 1);
     __syncthreads();
     int t = s_task;
     if (t >= n_tasks) break;
     int4 tk = solve_task(nT, t);
     int i = tk.y;
-    R acc = 0;
     bool fwd = tk.x == T_FWD;
+    // tile n (0 <= n < cnt) is an off-diagonal tile, tile cnt the inverse
+    int cnt = fwd ? i : nT - 1 - i;
+    auto tile_ptr = [&](int n) -> const R* {
+      if (n == cnt) return Linv + (size_t)i * kNB * kNB;
+      int jj = fwd ? n : nT - 1 - n;
+      return fwd ? A + (size_t)i * kNB * lda + (size_t)jj * kNB : A + (size_t)jj * kNB * lda + (size_t)i * kNB;
+    };
+    auto tile_ld = [&](int n) { return n == cnt ? kNB : lda; };
+    tile_async(buf0, tile_ptr(0), tile_ld(0));
+    R acc = 0;
     if (fwd) {
       acc = (R)b[i * kNB + r];
     } else {
@@ -402,26 +677,32 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
       if (!s_ok) break;
       acc = __ldcg(yw + i * kNB + r);
     }
-    int j0 = fwd ? 0 : nT - 1, j1 = fwd ? i : i, dj = fwd ? 1 : -1;
     bool ok = true;
-    for (int jj = j0; jj != j1; jj += dj) {
-      if (threadIdx.x == 0) s_ok = wait_ge((fwd ? sv.fdone : sv.bdone) + jj, 1, status);
-      __syncthreads();
-      if (!s_ok) {
-        ok = false;
-        break;
+    R out = 0;
+    for (int n = 0; n <= cnt; ++n) {
+      R* cur = (n & 1) ? buf1 : buf0;
+      if (n + 1 <= cnt) tile_async((n & 1) ? buf0 : buf1, tile_ptr(n + 1), tile_ld(n + 1));
+      else async_commit_empty();
+      if (n < cnt) {
+        int jj = fwd ? n : nT - 1 - n;
+        if (threadIdx.x == 0) s_ok = wait_ge((fwd ? sv.fdone : sv.bdone) + jj, 1, status);
+        __syncthreads();
+        if (!s_ok) {
+          ok = false;
+          break;
+        }
+        if (threadIdx.x < kNB) vin[threadIdx.x] = __ldcg(yw + jj * kNB + threadIdx.x);
+      } else if (part == 0) {
+        vin[r] = acc;
       }
-      if (fwd) load_tile(tile, A + (size_t)i * kNB * lda + (size_t)jj * kNB, lda);
-      else load_tile(tile, A + (size_t)jj * kNB * lda + (size_t)i * kNB, lda);
-      if (threadIdx.x < kNB) vin[threadIdx.x] = __ldcg(yw + jj * kNB + threadIdx.x);
+      async_wait_prev();
       __syncthreads();
-      acc -= tile_matvec(tile, vin, red, fwd ? 0 : 1);
+      R v = tile_matvec(cur, vin, red, fwd ? 0 : 1);
+      if (n < cnt) acc -= v;
+      else out = v;
     }
+    async_wait_all();
     if (!ok) break;
-    load_tile(tile, Linv + (size_t)i * kNB * kNB, kNB);
-    if (part == 0) vin[r] = acc;
-    __syncthreads();
-    R out = tile_matvec(tile, vin, red, fwd ? 0 : 1);
     if (part == 0) {
       __stcg(yw + i * kNB + r, out);
       if (!fwd) {
@@ -435,6 +716,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
       st_release((fwd ? sv.fdone : sv.bdone) + i, 1);
     }
   }
+  async_wait_all();
 }
 
 template <typename R>
@@ -442,7 +724,13 @@ cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* s
                               const double* b, R* bwork, double* x, int accumulate,
                               uint32_t* status, const LMState* lm, cudaStream_t st) {
   int n_tasks = 2 * nT;
-  size_t smem = sizeof(R) * (kNB * LD + kNB + 4 * kNB);
+  size_t smem = sizeof(R) * (2 * kNB * Pitch<R>::value + kNB + 4 * kNB);
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(R) == 8]) {
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_chol_solve<R>),
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set[sizeof(R) == 8] = true;
+  }
   SyncView sv(sync, nT);
   // reset the solve counter and the fwd/bwd flags
   cudaError_t e = cudaMemsetAsync(sv.sctr, 0, sizeof(int), st);

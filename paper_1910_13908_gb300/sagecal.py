@@ -273,11 +273,11 @@ def lm_normal_eqs(shape: Shape, R, C, jones, prec: int, ws):
     return JhJ, Jhr
 
 
-def lm_opts(n_lm=10, refine_sweeps=2, tau=1e-3, eps_grad=1e-12):
+def lm_opts(n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12):
     return LMOpts(int(n_lm), int(refine_sweeps), float(tau), float(eps_grad))
 
 
-def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_sweeps=2, tau=1e-3,
+def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_sweeps=1, tau=1e-3,
                   eps_grad=1e-12):
     """LM solve of one cluster; `jones` [N][2][2] complex128 is updated in place.
     Returns (jones, cost, iters) with cost/iters device scalars."""
@@ -296,7 +296,7 @@ def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_swee
 
 
 def calibrate_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, ws, n_em=1,
-                   n_lm=10, refine_sweeps=2, tau=1e-3, eps_grad=1e-12, costs=None):
+                   n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, costs=None):
     """The whole path for one job; `jones` [K][N][2][2] complex128 is updated in
     place.  Returns (jones, costs [K] device float64)."""
     import torch
