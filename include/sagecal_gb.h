@@ -119,6 +119,10 @@ typedef struct sc_lm_opts {
                             each float32 Cholesky solve (ignored for SC_FP64) */
   double tau;            /* mu0 = tau * max diag(J^T J) */
   double eps_grad;       /* stop once max|J^T r| <= eps_grad * (1 + cost) */
+  int32_t max_ctas;      /* cap on the thread blocks of the persistent
+                            factorisation kernel; 0 = enough to fill the GPU.
+                            Lower it when several jobs share the device. */
+  int32_t reserved;      /* must be 0 */
 } sc_lm_opts;
 
 typedef struct sc_sage_opts {
@@ -260,6 +264,34 @@ SC_API int32_t sc_calibrate_sage(const sc_dims* d, const double* uvw,
                                  const sc_sage_opts* opts, double* costs,
                                  int32_t prec, void* ws, size_t ws_bytes,
                                  void* stream);
+
+/* One job of a batch: the arguments of sc_calibrate_sage for one sub-band x
+ * time chunk, with its own workspace and stream (jobs may differ in every
+ * dimension). */
+typedef struct sc_job {
+  sc_dims dims;
+  const double* uvw;
+  const double* freqs;
+  sc_sky sky;
+  const void* V;
+  double* jones;
+  double* costs;
+  void* ws;
+  size_t ws_bytes;
+  void* stream;
+} sc_job;
+
+/* Many independent calibrations at once (paper §1: SAGECal distributes
+ * frequency bands; here sub-bands and time chunks of uneven size share one
+ * GPU).  Each job is calibrated exactly as by sc_calibrate_sage on its own
+ * stream with its own workspace; a pool of host threads enqueues them so
+ * that they overlap on the device, and the factorisation kernel of each job
+ * is capped (opts->lm.max_ctas, or an even share of the GPU when 0).  Results
+ * of a job do not depend on the other jobs.  Returns when every job has been
+ * enqueued; the first error (if any) is returned and later jobs are still
+ * attempted. */
+SC_API int32_t sc_calibrate_batch(const sc_job* jobs, int32_t n_jobs,
+                                  const sc_sage_opts* opts, int32_t prec);
 
 #ifdef __cplusplus
 }

@@ -3,7 +3,11 @@
 // job.  Everything is enqueued on the caller's stream; no call synchronises,
 // allocates or round-trips to the host between kernels.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
+#include <string>
+#include <thread>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 
@@ -165,6 +169,7 @@ static int check_lm(const sc_lm_opts* o) {
     return fail(SC_EINVAL, "n_lm must be >= 0 and refine_sweeps in [0, 16]");
   if (!(o->tau > 0)) return fail(SC_EINVAL, "tau must be > 0");
   if (!(o->eps_grad >= 0)) return fail(SC_EINVAL, "eps_grad must be >= 0");
+  if (o->max_ctas < 0 || o->reserved != 0) return fail(SC_EINVAL, "max_ctas must be >= 0 and reserved 0");
   return SC_OK;
 }
 
@@ -242,7 +247,7 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, H_cur, g_cur, cp_cur, J_cur, J_cur, c.st));
   for (int it = 0; it < o.n_lm; ++it) {
     SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, J_cur, H_cur, lm, A, true, false, c.st));
-    SC_LAUNCH(PK_CHOL, launch_chol<R>(A, L.Ppad, L.nT, Linv, sync, c.status(), lm, c.st));
+    SC_LAUNCH(PK_CHOL, launch_chol<R>(A, L.Ppad, L.nT, Linv, sync, c.status(), lm, o.max_ctas, c.st));
     SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, g_cur, bw, x, 0, c.status(), lm, c.st));
     if (mixed) {
       for (int sw = 0; sw < o.refine_sweeps; ++sw) {
@@ -470,6 +475,52 @@ SC_API int32_t sc_calibrate_sage(const sc_dims* d, const double* uvw, const doub
           ? sage<float>(c, uvw, freqs, sky, static_cast<const float*>(V), jones, *opts, costs)
           : sage<double>(c, uvw, freqs, sky, static_cast<const double*>(V), jones, *opts, costs);
   return r ? r : ok();
+}
+
+SC_API int32_t sc_calibrate_batch(const sc_job* jobs, int32_t n_jobs, const sc_sage_opts* opts, int32_t prec) {
+  if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return fail(SC_EINVAL, "bad job array");
+  if (!opts) return fail(SC_EINVAL, "options are NULL");
+  if (n_jobs == 0) return ok();
+  int dev = 0;
+  SC_CUDA(cudaGetDevice(&dev));
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  int workers = (int)std::min<unsigned>((unsigned)n_jobs, std::min(hw, 16u));
+  sc_sage_opts o = *opts;
+  if (o.lm.max_ctas == 0) o.lm.max_ctas = std::max(8, 2 * sms / workers);
+  std::atomic<int> next{0};
+  std::atomic<int> first_err{0};
+  std::vector<std::string> msgs(workers);
+  auto work = [&](int wid) {
+    cudaSetDevice(dev);
+    for (;;) {
+      int i = next.fetch_add(1);
+      if (i >= n_jobs) break;
+      const sc_job& j = jobs[i];
+      int r = sc_calibrate_sage(&j.dims, j.uvw, j.freqs, &j.sky, j.V, j.jones, &o, j.costs, prec, j.ws, j.ws_bytes,
+                                j.stream);
+      if (r != SC_OK) {
+        int z = 0;
+        if (first_err.compare_exchange_strong(z, r)) {
+          char buf[512];
+          sc_last_error(buf, sizeof(buf));
+          msgs[wid] = std::string("job ") + std::to_string(i) + ": " + buf;
+        }
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work, w);
+  work(0);
+  for (auto& t : pool) t.join();
+  int r = first_err.load();
+  if (r != SC_OK) {
+    for (auto& m : msgs)
+      if (!m.empty()) return fail(r, "%s", m.c_str());
+    return fail(r, "a job failed");
+  }
+  return ok();
 }
 
 }  // extern "C"

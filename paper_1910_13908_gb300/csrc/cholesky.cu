@@ -559,36 +559,38 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
   }
 }
 
+// Blocks of the persistent factorisation kernel that fill the GPU (at most
+// 4 per SM).  Computed once per precision; the function-local static makes
+// the first computation thread safe for concurrent callers.
 template <typename R>
 static int chol_grid(const void* fn, size_t smem) {
-  static int cached[2] = {0, 0};
-  int slot = sizeof(R) == 8 ? 1 : 0;
-  if (cached[slot] == 0) {
+  static const int cached = [&] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCholThreads, smem);
-    cached[slot] = std::max(1, sms * std::min(std::max(per, 1), 4));
-  }
-  return cached[slot];
+    return std::max(1, sms * std::min(std::max(per, 1), 4));
+  }();
+  return cached;
 }
 
 template <typename R>
 cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
-                        cudaStream_t st) {
+                        int max_ctas, cudaStream_t st) {
   int n_tasks = chol_ntasks(nT);
   size_t smem = sizeof(R) * (3 * kNB + 32) * Pitch<R>::value;
   const void* fn = reinterpret_cast<const void*>(&k_chol<R>);
   int grid = std::min(chol_grid<R>(fn, smem), n_tasks);
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
   cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * chol_factor_reset_ints(nT), st);
   if (e != cudaSuccess) return e;
   k_chol<R><<<grid, kCholThreads, smem, st>>>(A, lda, nT, Linv, n_tasks, sync, status, lm);
   return cudaGetLastError();
 }
-template cudaError_t launch_chol<float>(float*, int, int, float*, int*, uint32_t*, LMState*,
+template cudaError_t launch_chol<float>(float*, int, int, float*, int*, uint32_t*, LMState*, int,
                                         cudaStream_t);
-template cudaError_t launch_chol<double>(double*, int, int, double*, int*, uint32_t*, LMState*,
+template cudaError_t launch_chol<double>(double*, int, int, double*, int*, uint32_t*, LMState*, int,
                                          cudaStream_t);
 
 // ---- triangular solves ------------------------------------------------------------------------
@@ -725,12 +727,12 @@ cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* s
                               uint32_t* status, const LMState* lm, cudaStream_t st) {
   int n_tasks = 2 * nT;
   size_t smem = sizeof(R) * (2 * kNB * Pitch<R>::value + kNB + 4 * kNB);
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(R) == 8]) {
+  static const bool attr_set = [&] {
     cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_chol_solve<R>),
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set[sizeof(R) == 8] = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   SyncView sv(sync, nT);
   // reset the solve counter and the fwd/bwd flags
   cudaError_t e = cudaMemsetAsync(sv.sctr, 0, sizeof(int), st);

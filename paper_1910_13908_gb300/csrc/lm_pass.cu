@@ -126,8 +126,11 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
+// One block of 4 warps per station s: lanes stride over the other stations
+// o, form the baseline's contribution in float64 and accumulate in float64;
+// shuffles and one shared-memory step combine the 128 partial sums.
 template <typename R>
-__global__ void __launch_bounds__(256) k_station_reduce(int N, int64_t B, int nchunk,
+__global__ void __launch_bounds__(128) k_station_reduce(int N, int64_t B, int nchunk,
                                                         const R* __restrict__ stat_cost,
                                                         const R* __restrict__ stat_rho,
                                                         const R* __restrict__ w,
@@ -136,8 +139,9 @@ __global__ void __launch_bounds__(256) k_station_reduce(int N, int64_t B, int nc
                                                         double* __restrict__ cpart,
                                                         const LMState* __restrict__ lm) {
   if (lm != nullptr && (lm->done | lm->skip)) return;
-  __shared__ double sh[32];
+  __shared__ double part[4][13];
   int s = blockIdx.x;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc[13];
 #pragma unroll
   for (int i = 0; i < 13; ++i) acc[i] = 0.0;
@@ -166,13 +170,19 @@ __global__ void __launch_bounds__(256) k_station_reduce(int N, int64_t B, int nc
     acc[10] += wb * h01.re;
     acc[11] += wb * h01.im;
   }
-  double tot[13];
 #pragma unroll
-  for (int i = 0; i < 13; ++i) tot[i] = block_sum(acc[i], sh);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < 8; ++i) g[8 * s + i] = tot[i];
-    for (int i = 0; i < 4; ++i) H[4 * s + i] = tot[8 + i];
-    cpart[s] = tot[12];
+  for (int i = 0; i < 13; ++i) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+    if (lane == 0) part[warp][i] = acc[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < 13) {
+    int i = threadIdx.x;
+    double t = part[0][i] + part[1][i] + part[2][i] + part[3][i];
+    if (i < 8) g[8 * s + i] = t;
+    else if (i < 12) H[4 * s + i - 8] = t;
+    else cpart[s] = t;
   }
 }
 
@@ -180,7 +190,7 @@ template <typename R>
 cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
                                   int nchunk, const R* w, const double* J, double* g, double* H,
                                   double* cpart, const LMState* lm, cudaStream_t st) {
-  k_station_reduce<R><<<s.N, 256, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm);
+  k_station_reduce<R><<<s.N, 128, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm);
   return cudaGetLastError();
 }
 template cudaError_t launch_station_reduce<float>(const Shape&, const float*, const float*, int,

@@ -257,7 +257,7 @@ int chol_ntasks(int nT);
 int chol_sync_ints(int nT);
 template <typename R>
 cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
-                        cudaStream_t st);
+                        int max_ctas, cudaStream_t st);
 template <typename R>
 cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* sync,
                               const double* b, R* bwork, double* x, int accumulate,

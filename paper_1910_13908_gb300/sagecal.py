@@ -40,11 +40,18 @@ class SkyC(_c.Structure):
 
 class LMOpts(_c.Structure):
     _fields_ = [("n_lm", _c.c_int32), ("refine_sweeps", _c.c_int32),
-                ("tau", _c.c_double), ("eps_grad", _c.c_double)]
+                ("tau", _c.c_double), ("eps_grad", _c.c_double),
+                ("max_ctas", _c.c_int32), ("reserved", _c.c_int32)]
 
 
 class SageOpts(_c.Structure):
     _fields_ = [("n_em", _c.c_int32), ("lm", LMOpts)]
+
+
+class JobC(_c.Structure):
+    _fields_ = [("dims", Dims), ("uvw", _c.c_void_p), ("freqs", _c.c_void_p), ("sky", SkyC),
+                ("V", _c.c_void_p), ("jones", _c.c_void_p), ("costs", _c.c_void_p),
+                ("ws", _c.c_void_p), ("ws_bytes", _c.c_size_t), ("stream", _c.c_void_p)]
 
 
 def library_path() -> str:
@@ -73,6 +80,8 @@ def lib():
         L.sc_solve_cluster.argtypes = [D, vp, vp, vp, _c.POINTER(LMOpts), vp, vp, i32, vp, sz, vp]
         L.sc_calibrate_sage.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, vp, _c.POINTER(SageOpts),
                                         vp, i32, vp, sz, vp]
+        L.sc_calibrate_batch.argtypes = [_c.POINTER(JobC), i32, _c.POINTER(SageOpts), i32]
+        L.sc_calibrate_batch.restype = i32
         L.sc_launch_count.restype = _c.c_uint64
         L.sc_profile_read.argtypes = [i32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_double)]
         for f in ("sc_profile_begin", "sc_profile_end", "sc_profile_read"):
@@ -273,8 +282,8 @@ def lm_normal_eqs(shape: Shape, R, C, jones, prec: int, ws):
     return JhJ, Jhr
 
 
-def lm_opts(n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12):
-    return LMOpts(int(n_lm), int(refine_sweeps), float(tau), float(eps_grad))
+def lm_opts(n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, max_ctas=0):
+    return LMOpts(int(n_lm), int(refine_sweeps), float(tau), float(eps_grad), int(max_ctas), 0)
 
 
 def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_sweeps=1, tau=1e-3,
@@ -296,7 +305,7 @@ def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_swee
 
 
 def calibrate_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, ws, n_em=1,
-                   n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, costs=None):
+                   n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, costs=None, max_ctas=0):
     """The whole path for one job; `jones` [K][N][2][2] complex128 is updated in
     place.  Returns (jones, costs [K] device float64)."""
     import torch
@@ -308,9 +317,50 @@ def calibrate_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int
     _need(jones, torch.complex128, (K, d.N, 2, 2), "jones")
     if costs is None:
         costs = torch.zeros((K,), dtype=torch.float64, device=V.device)
-    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad))
+    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas))
     dc, skc = d.c(), sky.c()
     _check(lib().sc_calibrate_sage(_c.byref(dc), _ptr(uvw), _ptr(freqs), _c.byref(skc), _ptr(V),
                                    _ptr(jones), _c.byref(o), _ptr(costs), prec, _ptr(ws), ws.numel(),
                                    _stream()))
     return jones, costs
+
+
+@dataclasses.dataclass
+class Job:
+    """One calibration job of a batch: device inputs, in/out Jones, cost
+    output, its own workspace and its own stream."""
+    shape: Shape
+    uvw: object
+    freqs: object
+    sky: DeviceSky
+    V: object
+    jones: object
+    costs: object
+    ws: object
+    stream: object
+
+
+def calibrate_batch(jobs, prec: int, n_em=1, n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12,
+                    max_ctas=0):
+    """Enqueue every job (sc_calibrate_batch); each runs on job.stream.
+    Synchronise the streams (or the device) before reading the results."""
+    n = len(jobs)
+    arr = (JobC * n)()
+    keep = []
+    for i, j in enumerate(jobs):
+        K = j.sky.K
+        d = Shape(j.shape.N, j.shape.T, j.shape.F, K, max(j.shape.S_max, j.sky.S_max))
+        _need(j.V, _cdt(prec), (d.T, d.B, d.F, 2, 2), "V")
+        _need(j.jones, torch_complex128(), (K, d.N, 2, 2), "jones")
+        skc = j.sky.c()
+        keep.append(skc)
+        arr[i] = JobC(d.c(), _ptr(j.uvw), _ptr(j.freqs), skc, _ptr(j.V), _ptr(j.jones), _ptr(j.costs),
+                      _ptr(j.ws), j.ws.numel(), _c.c_void_p(j.stream.cuda_stream))
+    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas))
+    _check(lib().sc_calibrate_batch(arr, n, _c.byref(o), prec))
+    return jobs
+
+
+def torch_complex128():
+    import torch
+    return torch.complex128
