@@ -48,7 +48,30 @@ WORKLOADS = {
                                   "(spectral index -0.7), 10 clusters x 25 sources, 3 SAGE sweeps x 10 LM"),
     "lofar64": ("c1", 1, 10, "64 stations (2016 baselines), 10 timeslots, 1 channel at 150 MHz, "
                              "1 cluster x 20 sources, 10 LM"),
+    "serve500": ("c5", 3, 10, "Poisson-arriving calibration jobs: stations uniform in {64,128,256,384,512}, "
+                              "clusters 1-40 x 25 sources, 5-20 timeslots, 1-8 channels 140-160 MHz, 3 SAGE "
+                              "sweeps x 10 LM, continuous batching with HBM-footprint admission"),
+    "batch64": ("c3", 3, 10, "64 sub-band jobs of 256 stations (32640 baselines), timeslots uniform in 5-40 "
+                             "per job, 1 channel, 20 clusters x 50 sources, 3 SAGE sweeps x 10 LM, all jobs "
+                             "in one sc_calibrate_batch call"),
 }
+
+
+def job_seed(rank: int, i: int = 0) -> int:
+    """Seed of job i on rank `rank`: every rank calibrates its own, distinct
+    sub-band jobs (no data is shared between ranks)."""
+    return 1000 * rank + i
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time: all_reduce(MAX) of one float (any backend)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def peaks():
@@ -219,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     sc.lib()
     cfg, n_em, n_lm, desc = WORKLOADS[args.workload]
-    spec = synth.config(cfg, seed=rank)
+    spec = synth.config(cfg, seed=job_seed(rank))
     prec = sc.SC_FP64 if args.prec == "fp64" else sc.SC_MIXED
     job = make_job(spec, prec, dev)
     J = job["J0"].clone()
@@ -256,12 +279,7 @@ def run_ours(args, rank, world, local_rank):
     prof = sc.profile_end()
     n_launch = sc.launch_count() - n0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     value = units * args.steps * world / (ms / 1e3)
     final_costs = costs.cpu().numpy().tolist()
 
@@ -302,12 +320,7 @@ def run_ours(args, rank, world, local_rank):
             e2e_step()
         f1.record()
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(f0.elapsed_time(f1), world, dev)
         e2e = {"value": units * ks * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(bo), "steps": ks}
 
@@ -357,6 +370,165 @@ def run_ours(args, rank, world, local_rank):
         "fp64_gpu": fp64,
         "kernel_ms": breakdown,
         "final_costs_head": final_costs[:4],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_batch(args, rank, world, local_rank):
+    """One step = one sc_calibrate_batch call over 64 uneven jobs."""
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cfg, n_em, n_lm, desc = WORKLOADS["batch64"]
+    prec = sc.SC_FP64 if args.prec == "fp64" else sc.SC_MIXED
+    n_jobs = args.jobs
+    Ts = synth.uneven_time_chunks(n_jobs, 5, 40, seed=rank)
+    jobs, J0s, units = [], [], 0
+    for i in range(n_jobs):
+        spec = synth.config("c3", seed=job_seed(rank, i))
+        spec.T = int(Ts[i])
+        job = make_job(spec, prec, dev)
+        jobs.append(sc.Job(shape=job["shape"], uvw=job["uvw"], freqs=job["freqs"], sky=job["sky"], V=job["V"],
+                           jones=job["J0"].clone(), costs=torch.zeros(spec.K, dtype=torch.float64, device=dev),
+                           ws=job["ws"], stream=torch.cuda.Stream(dev)))
+        J0s.append(job["J0"])
+        units += spec.B * spec.T * spec.F * spec.K * n_lm * n_em
+    torch.cuda.synchronize()
+
+    def step():
+        for j, j0 in zip(jobs, J0s):
+            j.jones.copy_(j0)
+        torch.cuda.synchronize()
+        sc.calibrate_batch(jobs, prec, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    n0 = sc.launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    n_launch = sc.launch_count() - n0
+    clk = clocks.stop()
+    el = max_over_ranks(el, world, dev)
+    value = units * args.steps * world / el
+    pk, src = peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == sc.SC_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": "batch64", "description": desc, "jobs": n_jobs,
+                   "timeslots_per_job": [int(t) for t in Ts], "precision": args.prec,
+                   "timing": "host wall clock around each batch call with device synchronisation on both "
+                             "sides (the jobs run on 64 streams)",
+                   "l2": "inputs larger than L2"},
+        "gpu_launches": int(n_launch), "clocks": clk, "peak_kind": src,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def serve_spec(i, seed=0):
+    """Shape of serving job i (uniform draws from the serving workload)."""
+    u = synth.uniform(seed, synth.TAG_JOBS + 2, 5, offset=5 * i)
+    N = (64, 128, 256, 384, 512)[min(4, int(u[0] * 5))]
+    K = 1 + min(39, int(u[1] * 40))
+    T = 5 + min(15, int(u[2] * 16))
+    F = 1 + min(7, int(u[3] * 8))
+    return synth.JobSpec(N=N, T=T, F=F, K=K, S=25, f_lo=140e6, f_hi=160e6, seed=10000 + i)
+
+
+def host_job_from_gpu(i, spec, prec, dev):
+    """Host arrays of one serving job; its visibilities are simulated on the
+    GPU with the library's prediction (an input, not a result)."""
+    from paper_1910_13908_gb300 import serve
+    job = make_job(spec, prec, dev)
+    sky = job["sky_host"]
+    V = job["V"].cpu().numpy()
+    hj = serve.HostJob(i, sc_shape(spec), synth.station_uvw(spec), synth.freqs(spec), sky.l, sky.m, sky.flux,
+                       sky.alpha, [int(x) for x in sky.offsets], V, synth.identity_jones(spec.K, spec.N))
+    del job
+    return hj
+
+
+def sc_shape(spec):
+    from paper_1910_13908_gb300 import sagecal as sc
+    return sc.Shape(spec.N, spec.T, spec.F, spec.K, spec.S)
+
+
+def run_serve(args, rank, world, local_rank):
+    import queue
+    import threading
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc, serve
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cfg, n_em, n_lm, desc = WORKLOADS["serve500"]
+    prec = sc.SC_FP64 if args.prec == "fp64" else sc.SC_MIXED
+    n_jobs = args.jobs
+    specs = [serve_spec(i, seed=rank) for i in range(n_jobs)]
+    # single-stream capacity: a few jobs, one at a time
+    probe = serve.Server(prec=prec, max_slots=1, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
+    probe.start()
+    taus = []
+    for i in range(min(4, n_jobs)):
+        hj = host_job_from_gpu(100000 + i, specs[i], prec, dev)
+        t0 = time.perf_counter()
+        probe.submit(hj)
+        probe.drain()
+        taus.append(time.perf_counter() - t0)
+    probe.close()
+    tau = float(np.mean(taus))
+    rate = args.rate if args.rate > 0 else 0.8 / tau
+    # producer: host data of upcoming jobs, a few ahead
+    q = queue.Queue(maxsize=8)
+
+    def produce():
+        s = torch.cuda.Stream(dev)
+        with torch.cuda.stream(s):
+            for i, sp in enumerate(specs):
+                q.put(host_job_from_gpu(i, sp, prec, dev))
+    th = threading.Thread(target=produce, daemon=True)
+    th.start()
+    u = synth.uniform(rank, synth.TAG_JOBS + 3, n_jobs)
+    gaps = -np.log(u) / rate
+    arrivals = np.cumsum(gaps) - gaps[0]
+    srv = serve.Server(prec=prec, max_slots=args.slots, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
+    clocks = ClockSampler(local_rank)
+    n0 = sc.launch_count()
+    srv.start()
+    i = 0
+    while i < n_jobs or srv.step():
+        while i < n_jobs and srv.now() >= arrivals[i]:
+            srv.submit(q.get())
+            i += 1
+        srv.step()
+        time.sleep(0.0005)
+    st = srv.stats()
+    n_launch = sc.launch_count() - n0
+    clk = clocks.stop()
+    srv.close()
+    units = sum(sp.B * sp.T * sp.F * sp.K * n_lm * n_em for sp in specs)
+    value = units / st["span_s"]
+    line = {
+        "metric": METRIC + "; serving p50/p99 solve latency", "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * st["span_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == sc.SC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": "serve500", "description": desc, "jobs": n_jobs, "slots": args.slots,
+                   "arrival_rate_hz": rate, "single_stream_job_s": tau,
+                   "rate_rule": "0.8 x measured single-stream capacity" if args.rate <= 0 else "given"},
+        "serving": {"p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"], "mean_latency_s": st["mean_s"],
+                    "jobs_per_s": st["jobs_per_s"], "max_device_bytes_admitted": int(srv.max_used),
+                    "budget_bytes": int(srv.mem_budget)},
+        "gpu_launches": int(n_launch), "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -432,6 +604,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--jobs", type=int, default=0, help="jobs of the batch64 (64) / serve500 (500) workloads")
+    ap.add_argument("--slots", type=int, default=8, help="concurrent jobs of the serving workload")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (Hz); 0 = 0.8 x capacity")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -445,7 +620,14 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "batch64":
+            args.jobs = args.jobs or 64
+            run_batch(args, rank, world, local_rank)
+        elif args.workload == "serve500":
+            args.jobs = args.jobs or 500
+            run_serve(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist
