@@ -232,8 +232,14 @@ __device__ __forceinline__ void gemm_nt(double acc[4][4], const double* X, const
   }
 }
 
-__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+// Reciprocal of an elimination pivot: the hardware approximation (relative
+// error below 2^-22) in float32, the rounded reciprocal in float64.
+__device__ __forceinline__ float pivot_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double pivot_rcp(double x) { return __drcp_rn(x); }
 
 // Compile-time loops: every step below is instantiated with constant
 // indices, so the per-lane rows stay in registers.
@@ -251,157 +257,204 @@ struct Static<N, N> {
   __device__ __forceinline__ static void each(F&&) {}
 };
 
-// Cholesky of a 32x32 SPD block held by one warp, row i in lane i
-// (a[j] = A[i][j], j <= i read).  Pivots and column values move by
-// shuffles, no barrier.  On return a[j] = L[i][j] for j <= i and 0 above.
-// A non-positive pivot is replaced by 1 and sets *bad.
-template <typename R>
-__device__ __forceinline__ void warp_potrf32(R (&a)[32], int lane, int* bad) {
-  Static<0, 32>::each([&](auto cc) {
-    constexpr int c = decltype(cc)::value;
-    R p = __shfl_sync(0xffffffffu, a[c], c);
-    if (!(p > (R)0)) {
-      p = (R)1;
-      if (lane == 0) *bad = 1;
-    }
-    R rs = rsqrt(p);
-    R lic = (lane == c) ? p * rs : a[c] * rs;  // L[i][c] (meaningful for i >= c)
-    a[c] = lic;
-    Static<c + 1, 32>::each([&](auto jj) {
-      constexpr int j = decltype(jj)::value;
-      R ljc = __shfl_sync(0xffffffffu, lic, j);
-      if (lane >= j) a[j] -= lic * ljc;
-    });
-  });
-  Static<0, 32>::each([&](auto jj) {
-    constexpr int j = decltype(jj)::value;
-    if (j > lane) a[j] = 0;
-  });
-}
-
-// Inverse of a 32x32 lower-triangular L held one row per lane (l[j] =
-// L[i][j]); returns x[j] = (L^-1)[i][j].  Row operations on the identity:
-// after step m row m of the inverse is final and is broadcast by shuffles.
-template <typename R>
-__device__ __forceinline__ void warp_trinv32(const R (&l)[32], R (&x)[32], int lane) {
-  Static<0, 32>::each([&](auto jj) {
-    constexpr int j = decltype(jj)::value;
-    x[j] = (j == lane) ? (R)1 : (R)0;
-  });
-  Static<0, 32>::each([&](auto mm) {
-    constexpr int m = decltype(mm)::value;
-    R dinv = rcp_rn(__shfl_sync(0xffffffffu, l[m], m));
-    if (lane == m) {
-      Static<0, m + 1>::each([&](auto kk) {
-        constexpr int k = decltype(kk)::value;
-        x[k] *= dinv;
-      });
-    }
-    R lrm = l[m];  // L[lane][m]
-    Static<0, m + 1>::each([&](auto kk) {
-      constexpr int k = decltype(kk)::value;
-      R xmk = __shfl_sync(0xffffffffu, x[k], m);
-      if (lane > m) x[k] -= lrm * xmk;
-    });
-  });
-}
-
-// One warp: Cholesky and inverse of the 32x32 block at Ablk (pitch ld, lower
-// part read), writing L to Ablk and L^-1 to Xblk.  Kept out of line so that
-// the two calls of a tile factorisation share one copy of the fully
-// unrolled code (it runs once per panel, straight from the instruction
-// cache rather than L2).
-template <typename R>
-__device__ __noinline__ void warp_block32(R* Ablk, R* Xblk, int ld, int lane, int* bad) {
-  R a[32], x[32];
+// 16 consecutive values at a 16-byte aligned shared-memory address.
+__device__ __forceinline__ void ld16(const float* p, float (&v)[16]) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) a[j] = Ablk[lane * ld + j];
-  warp_potrf32(a, lane, bad);
-  warp_trinv32(a, x, lane);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    Ablk[lane * ld + j] = a[j];
-    Xblk[lane * ld + j] = x[j];
+  for (int u = 0; u < 4; ++u) {
+    float4 t = reinterpret_cast<const float4*>(p)[u];
+    v[4 * u] = t.x;
+    v[4 * u + 1] = t.y;
+    v[4 * u + 2] = t.z;
+    v[4 * u + 3] = t.w;
   }
 }
-
-// C[r][c] (+)= sign * sum_m X[r][m] Y[c][m] on 32x32 blocks in shared memory
-// (pitch ld), 256 threads, 2x2 outputs each.
-template <typename R>
-__device__ __forceinline__ void gemm32_nt(R* C, const R* X, const R* Y, int ld, R sign, bool accumulate) {
-  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  R acc[2][2] = {{0, 0}, {0, 0}};
-#pragma unroll 8
-  for (int m = 0; m < 32; ++m) {
-    R x0 = X[ty * ld + m], x1 = X[(ty + 16) * ld + m];
-    R y0 = Y[tx * ld + m], y1 = Y[(tx + 16) * ld + m];
-    acc[0][0] = fma(x0, y0, acc[0][0]);
-    acc[0][1] = fma(x0, y1, acc[0][1]);
-    acc[1][0] = fma(x1, y0, acc[1][0]);
-    acc[1][1] = fma(x1, y1, acc[1][1]);
+__device__ __forceinline__ void ld16(const double* p, double (&v)[16]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    double2 t = reinterpret_cast<const double2*>(p)[u];
+    v[2 * u] = t.x;
+    v[2 * u + 1] = t.y;
   }
+}
+__device__ __forceinline__ void st16(float* p, const float (&v)[16]) {
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int u = 0; u < 4; ++u)
+    reinterpret_cast<float4*>(p)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+}
+__device__ __forceinline__ void st16(double* p, const double (&v)[16]) {
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      R* p = C + (ty + 16 * a) * ld + tx + 16 * b;
-      *p = accumulate ? *p + sign * acc[a][b] : sign * acc[a][b];
-    }
+  for (int u = 0; u < 8; ++u) reinterpret_cast<double2*>(p)[u] = make_double2(v[2 * u], v[2 * u + 1]);
 }
 
-// In-place Cholesky of the 64x64 tile in sm (lower part read), writing L
-// (upper part zeroed) back to sm and Linv = L^-1 to sv, from 32x32 blocks:
-//   L11 = chol(A11), Linv11          warp 0, registers + shuffles
-//   L21 = A21 Linv11^T              whole CTA
-//   A22 -= L21 L21^T                whole CTA
-//   L22 = chol(A22), Linv22          warp 0
-//   Linv21 = -Linv22 (L21 Linv11)    whole CTA (via the scratch block W)
-// aux holds a 32x32 scratch block (pitch of the tile).
+// In-place Cholesky of the 64x64 SPD tile in sm (pitch of the tile, lower
+// part read), writing L (upper part zeroed) to sm and L^-1 to sv.
+//
+// Gaussian elimination in LDL^T form over the rows of [A | Y], Y = I at the
+// start, four columns per step.  With A = L' D L'^T (L' unit lower,
+// D = diag(p)), L = L' D^1/2 and L^-1 = D^-1/2 L'^-1; the elimination turns
+// Y into L'^-1.  Step k eliminates columns K = k..k+3 at once: with
+// V = A[:, K] and W = Y[K, :] as they stand before the step, and the 4x4
+// pivot block V[K, :] = L_D P L_D^T factorised by every thread, row i gets
+//   u_i = V[i, :] L_D^-T          (A[i][k+m] at step k+m: final for column k+m)
+//   g_i[m] = u_i[m] / p_m         (zero unless i > k+m)
+//   c_i = g_i L_D^-1
+//   A[i][j] -= c_i . V[j, :]      (j > k+3)
+//   Y[i][:] -= c_i . W            (equals the four single-column steps)
+// Afterwards L[i][j] = A[i][j] / sqrt(p_j) for j < i, L[j][j] = sqrt(p_j),
+// (L^-1)[i][c] = Y[i][c] / sqrt(p_i).  A non-positive pivot is replaced by
+// 1 and sets *bad.
+//
+// Thread layout: warp w owns column block q = w / 2 (columns 16q..16q+15)
+// of rows 32 (w & 1) .. +31, one row per lane, 16 entries of A and 16 of Y
+// in registers.  Each step reads the published columns K of A and rows K of
+// Y from shared memory (double-buffered, one barrier per step); the owners
+// of the next four columns and rows publish them.  aux holds 1088 scratch
+// values.
+template <typename R>
+__device__ __forceinline__ R pivot_guard(R p, int* bad) {
+  if (!(p > (R)0)) {
+    if (threadIdx.x == 0) *bad = 1;
+    return (R)1;
+  }
+  return p;
+}
+
 template <typename R>
 __device__ void potrf_tile(R* sm, R* sv, R* aux, int* bad) {
   constexpr int LD = Pitch<R>::value;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  R* A11 = sm;
-  R* A21 = sm + 32 * LD;
-  R* A22 = sm + 32 * LD + 32;
-  R* X11 = sv;
-  R* X21 = sv + 32 * LD;
-  R* X22 = sv + 32 * LD + 32;
-  R* W = aux;  // 32 x LD scratch
-  if (warp == 0) {
-    warp_block32(A11, X11, LD, lane, bad);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      sm[lane * LD + 32 + j] = 0;   // upper-right block of L
-      sv[lane * LD + 32 + j] = 0;   // upper-right block of Linv
-    }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp >> 1, i = 32 * (warp & 1) + lane, cb = 16 * q;
+  R* colb = aux;        // [2][4][64]: colb[m][j] = A[j][k+m]
+  R* rowb = aux + 512;  // [2][4][64]: rowb[m][c] = Y[k+m][c]
+  R* piv = aux + 1024;  // [64] pivots
+  R a[16], y[16];
+  ld16(sm + i * LD + cb, a);
+  Static<0, 16>::each([&](auto tt) {
+    constexpr int t = decltype(tt)::value;
+    y[t] = (cb + t == i) ? (R)1 : (R)0;
+  });
+  if (q == 0) {
+    colb[i] = a[0];
+    colb[64 + i] = a[1];
+    colb[128 + i] = a[2];
+    colb[192 + i] = a[3];
   }
+  if (i < 4) st16(rowb + 64 * i + cb, y);
   __syncthreads();
-  gemm32_nt(W, A21, X11, LD, (R)1, false);        // W = L21 = A21 Linv11^T
-  __syncthreads();
-  for (int e = tid; e < 32 * 32; e += blockDim.x) A21[(e >> 5) * LD + (e & 31)] = W[(e >> 5) * LD + (e & 31)];
-  __syncthreads();
-  gemm32_nt(A22, A21, A21, LD, (R)-1, true);      // A22 -= L21 L21^T
-  __syncthreads();
-  if (warp == 0) warp_block32(A22, X22, LD, lane, bad);
-  // W <- L21 Linv11 (note: X11 is lower; W[r][c] = sum_m L21[r][m] X11[m][c])
-  // computed as  sum_m L21[r][m] X11t[c][m]  with X11t = X11^T staged in X21
-  for (int e = tid; e < 32 * 32; e += blockDim.x) {
-    int r = e >> 5, c = e & 31;
-    X21[c * LD + r] = X11[r * LD + c];
+  for (int kb = 0; kb < 4; ++kb) {
+    Static<0, 4>::each([&](auto kq_) {
+      constexpr int kq = decltype(kq_)::value;
+      constexpr int bsel = kq & 1;  // parity of the step index 4 kb + kq
+      constexpr int t0 = 4 * kq;    // first column of K inside block q == kb
+      const int k = 16 * kb + t0;
+      const R* col = colb + 256 * bsel;
+      const R* row = rowb + 256 * bsel;
+      R* coln = colb + 256 * (bsel ^ 1);
+      R* rown = rowb + 256 * (bsel ^ 1);
+      // pivot block (lower part) and this row's entries in columns K
+      const R d00 = col[k], d10 = col[k + 1], d20 = col[k + 2], d30 = col[k + 3];
+      const R d11 = col[64 + k + 1], d21 = col[64 + k + 2], d31 = col[64 + k + 3];
+      const R d22 = col[128 + k + 2], d32 = col[128 + k + 3];
+      const R d33 = col[192 + k + 3];
+      const R x0 = col[i], x1 = col[64 + i], x2 = col[128 + i], x3 = col[192 + i];
+      // pivot block = L_D diag(p) L_D^T
+      const R p0 = pivot_guard(d00, bad), r0 = pivot_rcp(p0);
+      const R l10 = d10 * r0, l20 = d20 * r0, l30 = d30 * r0;
+      const R p1 = pivot_guard(fma(-l10, d10, d11), bad), r1 = pivot_rcp(p1);
+      const R e21 = fma(-l20, d10, d21), e31 = fma(-l30, d10, d31);
+      const R l21 = e21 * r1, l31 = e31 * r1;
+      const R p2 = pivot_guard(fma(-l21, e21, fma(-l20, d20, d22)), bad), r2 = pivot_rcp(p2);
+      const R e32 = fma(-l31, e21, fma(-l30, d20, d32));
+      const R l32 = e32 * r2;
+      const R p3 = pivot_guard(fma(-l32, e32, fma(-l31, e31, fma(-l30, d30, d33))), bad), r3 = pivot_rcp(p3);
+      if (threadIdx.x == 0) {
+        piv[k] = p0;
+        piv[k + 1] = p1;
+        piv[k + 2] = p2;
+        piv[k + 3] = p3;
+      }
+      // this row: u = V[i,:] L_D^-T, g = masked u / p, c = g L_D^-1
+      const R u0 = x0;
+      const R u1 = fma(-l10, u0, x1);
+      const R u2 = fma(-l21, u1, fma(-l20, u0, x2));
+      const R u3 = fma(-l32, u2, fma(-l31, u1, fma(-l30, u0, x3)));
+      const R g0 = i > k ? u0 * r0 : (R)0;
+      const R g1 = i > k + 1 ? u1 * r1 : (R)0;
+      const R g2 = i > k + 2 ? u2 * r2 : (R)0;
+      const R g3 = i > k + 3 ? u3 * r3 : (R)0;
+      const R c3 = g3;
+      const R c2 = fma(-c3, l32, g2);
+      const R c1 = fma(-c3, l31, fma(-c2, l21, g1));
+      const R c0 = fma(-c3, l30, fma(-c2, l20, fma(-c1, l10, g0)));
+      // A[i][j] -= c . V[j,:] for the columns j > k+3 of this block
+      if (q >= kb) {
+        R v0[16], v1[16], v2[16], v3[16];
+        ld16(col + cb, v0);
+        ld16(col + 64 + cb, v1);
+        ld16(col + 128 + cb, v2);
+        ld16(col + 192 + cb, v3);
+        if (q > kb) {
+          Static<0, 16>::each([&](auto tt) {
+            constexpr int t = decltype(tt)::value;
+            a[t] = fma(-c3, v3[t], fma(-c2, v2[t], fma(-c1, v1[t], fma(-c0, v0[t], a[t]))));
+          });
+        } else {
+          a[t0] = u0;
+          a[t0 + 1] = u1;
+          a[t0 + 2] = u2;
+          a[t0 + 3] = u3;
+          Static<t0 + 4, 16>::each([&](auto tt) {
+            constexpr int t = decltype(tt)::value;
+            a[t] = fma(-c3, v3[t], fma(-c2, v2[t], fma(-c1, v1[t], fma(-c0, v0[t], a[t]))));
+          });
+        }
+      }
+      // Y[i][:] -= c . W; W[m][col] is zero right of column k+m
+      if (q <= kb) {
+        R w0[16], w1[16], w2[16], w3[16];
+        ld16(row + cb, w0);
+        ld16(row + 64 + cb, w1);
+        ld16(row + 128 + cb, w2);
+        ld16(row + 192 + cb, w3);
+        Static<0, 16>::each([&](auto tt) {
+          constexpr int t = decltype(tt)::value;
+          y[t] = fma(-c3, w3[t], fma(-c2, w2[t], fma(-c1, w1[t], fma(-c0, w0[t], y[t]))));
+        });
+      }
+      // publish the next four columns of A and rows of Y
+      if (k + 4 < 64) {
+        if constexpr (kq < 3) {
+          if (q == kb) {
+            coln[i] = a[t0 + 4];
+            coln[64 + i] = a[t0 + 5];
+            coln[128 + i] = a[t0 + 6];
+            coln[192 + i] = a[t0 + 7];
+          }
+        } else {
+          if (q == kb + 1) {
+            coln[i] = a[0];
+            coln[64 + i] = a[1];
+            coln[128 + i] = a[2];
+            coln[192 + i] = a[3];
+          }
+        }
+        if (i >= k + 4 && i < k + 8) st16(rown + 64 * (i - k - 4) + cb, y);
+      }
+      __syncthreads();
+    });
   }
-  __syncthreads();
-  gemm32_nt(W, A21, X21, LD, (R)1, false);        // W = L21 Linv11
-  __syncthreads();
-  // X21 <- -Linv22 W : sum_m X22[r][m] W[m][c]; stage W^T in X21 first
-  for (int e = tid; e < 32 * 32; e += blockDim.x) {
-    int r = e >> 5, c = e & 31;
-    X21[c * LD + r] = W[r * LD + c];
-  }
-  __syncthreads();
-  gemm32_nt(W, X22, X21, LD, (R)-1, false);       // W = -Linv22 (L21 Linv11)
-  __syncthreads();
-  for (int e = tid; e < 32 * 32; e += blockDim.x) X21[(e >> 5) * LD + (e & 31)] = W[(e >> 5) * LD + (e & 31)];
+  R pj[16];
+  ld16(piv + cb, pj);
+  const R ri = rsqrt(piv[i]);
+  Static<0, 16>::each([&](auto tt) {
+    constexpr int t = decltype(tt)::value;
+    const int j = cb + t;
+    const R rj = rsqrt(pj[t]);
+    a[t] = j < i ? a[t] * rj : (j == i ? pj[t] * rj : (R)0);
+    y[t] = j <= i ? y[t] * ri : (R)0;
+  });
+  st16(sm + i * LD + cb, a);
+  st16(sv + i * LD + cb, y);
   __syncthreads();
 }
 
