@@ -56,41 +56,48 @@ static int chol_factor_reset_ints(int nT) { return 2 + 2 * nT * nT + nT; }
 //   POTRF(j+1), TRSM(j+2..nT-1, j+1)
 //   UPDATE(i, k, j) for k = j+2..nT-1, i = k..nT-1
 // Returned as (type, i, k, j); type -1 past the end.
+// Tasks in the panel blocks whose size parameter m (= nT - 1 - j) runs from
+// 1 to x: block j holds m + 1 + (m - 1) + (m - 1) m / 2 = (m^2 + 3m) / 2
+// tasks, and the sum of (m^2 + 3m) / 2 over m = 1..x is x (x+1) (x+5) / 6.
+__host__ __device__ __forceinline__ long long chol_panel_tasks(long long x) { return x * (x + 1) * (x + 5) / 6; }
+
+// Decodes list position t in O(1): the panel block from a cube-root estimate
+// of the inverse of chol_panel_tasks, the trailing-update column from the
+// quadratic formula, each estimate corrected by exact integer comparisons.
 __host__ __device__ int4 chol_task(int nT, int t) {
   if (t == 0) return make_int4(T_POTRF, 0, 0, 0);
-  t -= 1;
-  if (t < nT - 1) return make_int4(T_TRSM, t + 1, 0, 0);
-  t -= nT - 1;
-  for (int j = 0; j + 1 < nT; ++j) {
-    int m = nT - j - 1, m2 = nT - j - 2;
-    int block = m + 1 + m2 + m2 * (m2 + 1) / 2;
-    if (t >= block) {
-      t -= block;
-      continue;
-    }
-    if (t < m) return make_int4(T_UPD, j + 1 + t, j + 1, j);
-    t -= m;
-    if (t == 0) return make_int4(T_POTRF, j + 1, j + 1, j + 1);
-    t -= 1;
-    if (t < m2) return make_int4(T_TRSM, j + 2 + t, j + 1, j + 1);
-    t -= m2;
-    for (int k = j + 2; k < nT; ++k) {
-      int c = nT - k;
-      if (t < c) return make_int4(T_UPD, k + t, k, j);
-      t -= c;
-    }
-  }
-  return make_int4(-1, 0, 0, 0);
+  if (t < nT) return make_int4(T_TRSM, t, 0, 0);
+  const long long r = (long long)t - nT;  // rank among the panel blocks
+  const long long total = chol_panel_tasks(nT - 1);
+  if (r >= total) return make_int4(-1, 0, 0, 0);
+  // block with the smallest m such that the blocks m..1 hold >= total - r tasks
+  const long long left = total - r;
+  int m = (int)cbrtf(6.0f * (float)left);
+  if (m < 1) m = 1;
+  if (m > nT - 1) m = nT - 1;
+  while (chol_panel_tasks(m) < left) ++m;
+  while (m > 1 && chol_panel_tasks(m - 1) >= left) --m;
+  const int j = nT - 1 - m, m2 = m - 1;
+  int rel = (int)(r - (total - chol_panel_tasks(m)));
+  if (rel < m) return make_int4(T_UPD, j + 1 + rel, j + 1, j);
+  rel -= m;
+  if (rel == 0) return make_int4(T_POTRF, j + 1, j + 1, j + 1);
+  rel -= 1;
+  if (rel < m2) return make_int4(T_TRSM, j + 2 + rel, j + 1, j + 1);
+  rel -= m2;
+  // trailing columns k = j+2.. hold m2, m2-1, ... tasks; column n starts at
+  // n m2 - n (n-1) / 2
+  const float bq = 2.0f * m2 + 1.0f;
+  int n = (int)((bq - sqrtf(fmaxf(bq * bq - 8.0f * rel, 0.0f))) * 0.5f);
+  if (n < 0) n = 0;
+  auto start = [m2](int c) { return c * m2 - c * (c - 1) / 2; };
+  while (n > 0 && start(n) > rel) --n;
+  while (n + 1 < m2 && start(n + 1) <= rel) ++n;
+  const int k = j + 2 + n;
+  return make_int4(T_UPD, k + (rel - start(n)), k, j);
 }
 
-int chol_ntasks(int nT) {
-  int n = nT;  // POTRF(0) + TRSM(1..nT-1, 0)
-  for (int j = 0; j + 1 < nT; ++j) {
-    int m = nT - j - 1, m2 = nT - j - 2;
-    n += m + 1 + m2 + m2 * (m2 + 1) / 2;
-  }
-  return n;
-}
+int chol_ntasks(int nT) { return nT + (int)chol_panel_tasks(nT - 1); }
 
 // Solve list: FWD(0..nT-1), then BWD(nT-1..0).
 __host__ __device__ int4 solve_task(int nT, int t) {
@@ -108,6 +115,9 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+// Publishes a counter.  Callers reach it through a __syncthreads() after
+// the block's stores of the tile; a release store is cumulative, so those
+// stores of every thread of the block become visible before the counter.
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -121,28 +131,22 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
   return v;
 }
 
-// Waits until *p >= v.  Polls with relaxed loads (an acquire load on every
-// poll would invalidate this SM's L1 each time and stall the load/store
-// path of the other CTAs sharing the SM) and takes one acquire fence once
-// the counter is seen.  Gives up (returns false) after kSpinLimit polls or
-// as soon as another CTA has recorded a timeout.
+// Waits until *p >= v (the counters only grow).  The first read is an
+// acquire load, which settles the common case of a dependency finished long
+// ago in one round trip.  Otherwise it polls with relaxed loads (an acquire
+// load on every poll would invalidate this SM's L1 each time and stall the
+// load/store path of the other CTAs sharing the SM) and confirms with one
+// acquire load once the value is seen.  An acquire load, unlike a fence,
+// does not wait for this thread's earlier stores and atomics to complete.
+// Gives up (returns false) after kSpinLimit polls or as soon as another
+// CTA has recorded a timeout.
 __device__ bool wait_ge(const int* p, int v, uint32_t* status) {
-#ifdef SC_SPIN_ACQUIRE
+  if (ld_acquire(p) >= v) return true;
   for (long it = 0; it < kSpinLimit; ++it) {
-    if (ld_acquire(p) >= v) return true;
-    if ((it & 63) == 63 && (ld_status(status) & SC_STATUS_TIMEOUT)) return false;
     __nanosleep(it < 16 ? 32 : 200);
-  }
-#else
-  for (long it = 0; it < kSpinLimit; ++it) {
-    if (ld_relaxed(p) >= v) {
-      asm volatile("fence.acq_rel.gpu;" ::: "memory");
-      return true;
-    }
+    if (ld_relaxed(p) >= v) return ld_acquire(p) >= v;
     if ((it & 63) == 63 && (ld_status(status) & SC_STATUS_TIMEOUT)) return false;
-    __nanosleep(it < 16 ? 32 : 200);
   }
-#endif
   atomicOr(status, SC_STATUS_TIMEOUT);
   return false;
 }
@@ -170,6 +174,23 @@ __device__ __forceinline__ void load_tile(R* sm, const R* g, int lda) {
     *reinterpret_cast<float4*>(sm + r * LD + c) = v;
   }
 }
+// The same copy issued as 16-byte cp.async requests (L2 only); the caller
+// commits the group.
+template <typename R>
+__device__ __forceinline__ void copy_tile_async(R* sm, const R* g, int lda) {
+  constexpr int LD = Pitch<R>::value;
+  constexpr int PER_ROW = kNB * (int)sizeof(R) / 16;
+  for (int e = threadIdx.x; e < kNB * PER_ROW; e += blockDim.x) {
+    int r = e / PER_ROW, ch = e - r * PER_ROW;
+    const char* src = reinterpret_cast<const char*>(g + (size_t)r * lda) + 16 * ch;
+    unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char*>(sm + r * LD) + 16 * ch);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  }
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <typename R>
 __device__ __forceinline__ void store_tile(R* g, int lda, const R* sm) {
   constexpr int LD = Pitch<R>::value;
@@ -491,7 +512,6 @@ __device__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32
         atomicOr(status, SC_STATUS_NOTPD);
         if (lm != nullptr) lm->notpd = 1;
       }
-      __threadfence();
       st_release(sv.pdone + j, 1);
     }
     if (j + 1 == nT) break;
@@ -518,7 +538,6 @@ __device__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32
       }
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
       st_release(sv.tdone + (j + 1) * nT + j, 1);
     }
     // UPDATE(j+1, j+1, j): the next diagonal tile, kept in T0 for POTRF(j+1)
@@ -538,6 +557,42 @@ __device__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32
   }
 }
 
+// Dependency counter q (0..2) of a TRSM or UPDATE task and the value it
+// must reach; p = nullptr where the task has fewer counters.
+__device__ __forceinline__ void task_dep(int4 tk, int nT, const SyncView& sv, int q, const int*& p, int& v) {
+  const int i = tk.y, k = tk.z, j = tk.w;
+  p = nullptr;
+  v = 0;
+  if (tk.x == T_TRSM) {
+    if (q == 0) p = sv.pdone + j, v = 1;
+    else if (q == 1) p = sv.upd + i * nT + j, v = j;
+  } else {
+    if (q == 0) p = sv.tdone + i * nT + j, v = 1;
+    else if (q == 1) p = sv.tdone + k * nT + j, v = 1;
+    else p = sv.upd + i * nT + k, v = j;
+  }
+}
+
+// Queues the operand tiles of a TRSM (A_ij, Linv_jj) or UPDATE (L_ij, L_kj)
+// task into X and Y as one cp.async group.
+template <typename R>
+__device__ __forceinline__ void task_operands_async(int4 tk, const R* A, int lda, const R* Linv, R* X, R* Y) {
+  const int i = tk.y, k = tk.z, j = tk.w;
+  copy_tile_async(X, A + (size_t)i * kNB * lda + (size_t)j * kNB, lda);
+  if (tk.x == T_TRSM) copy_tile_async(Y, Linv + (size_t)j * kNB * kNB, kNB);
+  else copy_tile_async(Y, A + (size_t)k * kNB * lda + (size_t)j * kNB, lda);
+  async_commit();
+}
+
+// Persistent tile-DAG factorisation.  Block 0's first claim is task 0: it
+// becomes the walker.  Every other block runs TRSM and UPDATE tasks in
+// list order, two deep: while it multiplies the current task, the operands
+// of the task it claimed next are already on their way into the other
+// buffer pair, provided that task's dependencies were complete when it
+// looked (a non-blocking check); otherwise it finishes the current task
+// first and then waits.  The lowest unfinished claimed task is always some
+// block's current task, whose dependencies precede it in the list, so list
+// order rules out deadlock.
 template <typename R>
 __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int lda, int nT,
                                                       R* __restrict__ Linv, int n_tasks,
@@ -548,78 +603,121 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
   R* s0 = reinterpret_cast<R*>(smraw);
   R* s1 = s0 + kNB * LD;
   R* s2 = s1 + kNB * LD;
-  R* aux = s2 + kNB * LD;
+  R* aux = s2 + kNB * LD;  // the walker's scratch; the second Y buffer otherwise
+  auto Xb = [&](int b) { return b ? s2 : s0; };  // buffer pairs (s0, s1) and (s2, aux)
+  auto Yb = [&](int b) { return b ? aux : s1; };
   __shared__ int s_task, s_ok, s_bad;
   SyncView sv(sync, nT);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int next = -1;  // thread 0: the claimed, not yet examined task
+  // The walker publishes its SM (+1) in the otherwise idle solve counter; a
+  // block sharing that SM stops claiming, finishes what it holds and
+  // leaves the SM to the critical path.  A hint only: nothing depends on it.
+  int walker_sm = -1, my_sm = 0;
+  if (threadIdx.x == 0) asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
+  auto claim = [&]() -> int {  // thread 0
+    if (walker_sm < 0) {
+      const int w = ld_relaxed(sv.sctr);
+      if (w > 0) walker_sm = w - 1;
+    }
+    return walker_sm == my_sm ? n_tasks : atomicAdd(sv.fctr, 1);
+  };
+  int4 cur = make_int4(-1, 0, 0, 0);
+  bool have = false;  // cur's operands are queued in buffer pair buf
+  int buf = 0;
   for (;;) {
-    __syncthreads();  // every thread has read the previous s_task
-    if (threadIdx.x == 0) s_task = atomicAdd(sv.fctr, 1);
-    __syncthreads();
-    int t = s_task;
-    if (t >= n_tasks) break;
-    if (t == 0) {
-      chol_walker(A, lda, nT, Linv, sv, status, lm, s0, s1, s2, aux, &s_bad, &s_ok);
-      break;
+    if (!have) {
+      // claim tasks until one is ours, then wait for its dependencies
+      __syncthreads();  // every thread has read the previous s_task
+      if (threadIdx.x == 0) {
+        s_task = next >= 0 ? next : claim();
+        next = -1;
+      }
+      __syncthreads();
+      const int t = s_task;
+      if (t >= n_tasks) break;
+      if (t == 0) {
+        if (threadIdx.x == 0) st_release(sv.sctr, my_sm + 1);
+        chol_walker(A, lda, nT, Linv, sv, status, lm, s0, s1, s2, aux, &s_bad, &s_ok);
+        break;
+      }
+      cur = chol_task(nT, t);
+      if (walker_task(cur)) continue;
+      if (threadIdx.x == 0) next = claim();
+      bool ok = true;
+      if (threadIdx.x < 3) {
+        const int* p;
+        int v;
+        task_dep(cur, nT, sv, threadIdx.x, p, v);
+        if (p != nullptr) ok = wait_ge(p, v, status);
+      }
+      if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
+        break;
+      }
+      task_operands_async(cur, A, lda, Linv, Xb(buf), Yb(buf));
+      have = true;
     }
-    int4 tk = chol_task(nT, t);
-    if (walker_task(tk)) continue;
-    int i = tk.y, k = tk.z, j = tk.w;
-    if (threadIdx.x == 0) {
-      bool ok;
-      if (tk.x == T_TRSM) {
-        ok = wait_ge(sv.pdone + j, 1, status) && wait_ge(sv.upd + i * nT + j, j, status);
+    // look at the claimed next task; queue its operands if it is ready
+    if (threadIdx.x == 0) s_task = next;
+    __syncthreads();
+    const int t2 = s_task;
+    int4 nxt = make_int4(-1, 0, 0, 0);
+    bool staged = false;
+    if (t2 >= 0 && t2 < n_tasks) {
+      nxt = chol_task(nT, t2);
+      if (walker_task(nxt)) {
+        if (threadIdx.x == 0) next = -1;  // done by the walker: skip it
       } else {
-        ok = wait_ge(sv.tdone + i * nT + j, 1, status) && wait_ge(sv.tdone + k * nT + j, 1, status) &&
-             wait_ge(sv.upd + i * nT + k, j, status);
+        bool ready = true;
+        if (threadIdx.x < 3) {
+          const int* p;
+          int v;
+          task_dep(nxt, nT, sv, threadIdx.x, p, v);
+          if (p != nullptr) ready = ld_acquire(p) >= v;
+        }
+        staged = __syncthreads_and(ready) != 0;
+        if (staged) {
+          if (threadIdx.x == 0) next = claim();
+          task_operands_async(nxt, A, lda, Linv, Xb(buf ^ 1), Yb(buf ^ 1));
+        }
       }
-      s_ok = ok;
     }
+    // the current task
+    const int i = cur.y, k = cur.z, j = cur.w;
+    const bool trsm = cur.x == T_TRSM;
+    R* Out = A + (size_t)i * kNB * lda + (size_t)(trsm ? j : k) * kNB;
+    R old[4][4];  // an UPDATE's output tile, fetched while the operands arrive
+    if (!trsm) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) old[a][b] = __ldcg(Out + (size_t)(ty + 16 * a) * lda + tx + 16 * b);
+    }
+    if (staged) async_wait_prev();
+    else async_wait_all();
     __syncthreads();
-    if (!s_ok) {
-      if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
-      break;
-    }
-    int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     R acc[4][4];
-    if (tk.x == T_TRSM) {
-      R* Aij = A + (size_t)i * kNB * lda + (size_t)j * kNB;
-      load_tile(s0, Aij, lda);
-      load_tile(s1, Linv + (size_t)j * kNB * kNB, kNB);
-      __syncthreads();
-      gemm_nt(acc, s0, s1);
+    gemm_nt(acc, Xb(buf), Yb(buf));
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) __stcg(Aij + (size_t)(ty + 16 * a) * lda + tx + 16 * b, acc[a][b]);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(sv.tdone + i * nT + j, 1);
-      }
+      for (int b = 0; b < 4; ++b)
+        __stcg(Out + (size_t)(ty + 16 * a) * lda + tx + 16 * b, trsm ? acc[a][b] : old[a][b] - acc[a][b]);
+    __syncthreads();  // the tile is stored and buffer pair buf is free
+    // published by a thread outside warp 0, whose lanes 0..2 go on polling
+    if (threadIdx.x == 32) {
+      if (trsm) st_release(sv.tdone + i * nT + j, 1);
+      else st_release(sv.upd + i * nT + k, j + 1);
+    }
+    if (staged) {
+      cur = nxt;
+      buf ^= 1;
     } else {
-      const R* Lij = A + (size_t)i * kNB * lda + (size_t)j * kNB;
-      const R* Lkj = A + (size_t)k * kNB * lda + (size_t)j * kNB;
-      R* Aik = A + (size_t)i * kNB * lda + (size_t)k * kNB;
-      R old[4][4];  // the output tile, fetched while the operands load and multiply
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) old[a][b] = __ldcg(Aik + (size_t)(ty + 16 * a) * lda + tx + 16 * b);
-      load_tile(s0, Lij, lda);
-      load_tile(s1, Lkj, lda);
-      __syncthreads();
-      gemm_nt(acc, s0, s1);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) __stcg(Aik + (size_t)(ty + 16 * a) * lda + tx + 16 * b, old[a][b] - acc[a][b]);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(sv.upd + i * nT + k, j + 1);
-      }
+      have = false;
     }
   }
+  async_wait_all();
 }
 
 // Blocks of the persistent factorisation kernel that fill the GPU (at most
@@ -642,7 +740,7 @@ template <typename R>
 cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
                         int max_ctas, cudaStream_t st) {
   int n_tasks = chol_ntasks(nT);
-  size_t smem = sizeof(R) * (3 * kNB + 32) * Pitch<R>::value;
+  size_t smem = sizeof(R) * (4 * kNB) * Pitch<R>::value;  // two buffer pairs; the walker uses 3.5 tiles
   const void* fn = reinterpret_cast<const void*>(&k_chol<R>);
   int grid = std::min(chol_grid<R>(fn, smem), n_tasks);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
@@ -658,23 +756,13 @@ template cudaError_t launch_chol<double>(double*, int, int, double*, int*, uint3
 
 // ---- triangular solves ------------------------------------------------------------------------
 
-// Asynchronous copy of one 64x64 tile into shared memory (16-byte cp.async,
-// L2 only), as one commit group.
+// Asynchronous copy of one 64x64 tile into shared memory as one commit group.
 template <typename R>
 __device__ __forceinline__ void tile_async(R* sm, const R* g, int lda) {
-  constexpr int LD = Pitch<R>::value;
-  constexpr int PER_ROW = kNB * (int)sizeof(R) / 16;
-  for (int e = threadIdx.x; e < kNB * PER_ROW; e += blockDim.x) {
-    int r = e / PER_ROW, ch = e - r * PER_ROW;
-    const char* src = reinterpret_cast<const char*>(g + (size_t)r * lda) + 16 * ch;
-    unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char*>(sm + r * LD) + 16 * ch);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
+  copy_tile_async(sm, g, lda);
+  async_commit();
 }
-__device__ __forceinline__ void async_commit_empty() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void async_commit_empty() { async_commit(); }
 
 // out[r] = sum_m T[r][m] v[m] (trans = 0) or sum_m T[m][r] v[m] (trans = 1) for a
 // 64x64 tile in shared memory; 4 threads per r, combined through red[4][64].
@@ -777,7 +865,6 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
       st_release((fwd ? sv.fdone : sv.bdone) + i, 1);
     }
   }

@@ -50,6 +50,27 @@ def test_host_only_calls(lib):
         sagecal.workspace_size(sagecal.Shape(N=8, T=10, F=1), 7)
 
 
+def _documented_order(nT):
+    """The factorisation list spelled out loop by loop: POTRF(0) and the
+    TRSMs of column 0, then for each panel j the next column's updates,
+    POTRF(j+1), the TRSMs of column j+1 and the remaining trailing updates."""
+    out = [(0, 0, 0, 0)] + [(1, i, 0, 0) for i in range(1, nT)]
+    for j in range(nT - 1):
+        out += [(2, i, j + 1, j) for i in range(j + 1, nT)]
+        out.append((0, j + 1, j + 1, j + 1))
+        out += [(1, i, j + 1, j + 1) for i in range(j + 2, nT)]
+        out += [(2, i, k, j) for k in range(j + 2, nT) for i in range(k, nT)]
+    return out
+
+
+def test_cholesky_task_decoder_matches_documented_order():
+    """The closed-form decoder of list positions reproduces the documented
+    loop order exactly, including orders far above the test sizes (the
+    cube-root and quadratic estimates are corrected by exact comparisons)."""
+    for nT in list(range(1, 40)) + [63, 64, 65, 100, 128, 129, 200]:
+        assert [tuple(t) for t in sagecal.chol_schedule(nT, 0)] == _documented_order(nT), nT
+
+
 def test_cholesky_task_order_respects_every_dependency():
     """Every task's inputs are produced by tasks earlier in the list, each
     tile receives its updates in panel order, and the list covers the
