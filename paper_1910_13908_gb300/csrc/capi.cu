@@ -95,7 +95,7 @@ Workspace plan_workspace(const Shape& s, bool job) {
   L.x = take((size_t)L.Ppad * 8);
   L.rvec = take((size_t)L.Ppad * 8);
   L.corr = take((size_t)L.Ppad * 8);
-  L.bvec = take((size_t)L.Ppad * rs);
+  L.bvec = take((size_t)L.Ppad * 2 * rs);
   L.A = take((size_t)L.Ppad * L.Ppad * rs);
   L.Linv = take((size_t)L.nT * kNB * kNB * rs);
   L.sync = take((size_t)chol_sync_ints(L.nT) * 4);
@@ -232,7 +232,7 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   R* str = c.at<R>(L.stat_rho);
   R* A = c.at<R>(L.A);
   R* Linv = c.at<R>(L.Linv);
-  R* bw = c.at<R>(L.bvec);
+  uint64_t* bw = c.at<uint64_t>(L.bvec);
   int* sync = c.at<int>(L.sync);
   LMState* lm = c.lm();
   const int flags = running ? (P_OLD | P_SUB | P_STATS) : (P_SUB | P_STATS);
@@ -242,6 +242,7 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   SC_CUDA(cudaMemcpyAsync(J_cur, J_io, n8, cudaMemcpyDeviceToDevice, c.st));
   SC_CUDA(cudaMemsetAsync(x, 0, (size_t)L.Ppad * sizeof(double), c.st));
   SC_CUDA(cudaMemsetAsync(rvec, 0, (size_t)L.Ppad * sizeof(double), c.st));
+  SC_CUDA(cudaMemsetAsync(bw, 0, (size_t)L.Ppad * 2 * sizeof(R), c.st));  // no stale tag can match
   SC_LAUNCH(PK_PASS, launch_pass<R>(s, flags, Xin, C, J_old, J_cur, nullptr, stc, str, L.nchunk, L.tchunk, nullptr, c.st));
   SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_cur, g_cur, H_cur, cp_cur, nullptr, c.st));
   SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, H_cur, g_cur, cp_cur, J_cur, J_cur, c.st));

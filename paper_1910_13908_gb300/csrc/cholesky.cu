@@ -23,6 +23,7 @@
 // (ld.global.cg / st.global.cg), and published with a fence followed by a
 // release store of the tile's counter.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "sc_common.cuh"
@@ -764,141 +765,260 @@ __device__ __forceinline__ void tile_async(R* sm, const R* g, int lda) {
 }
 __device__ __forceinline__ void async_commit_empty() { async_commit(); }
 
-// out[r] = sum_m T[r][m] v[m] (trans = 0) or sum_m T[m][r] v[m] (trans = 1) for a
-// 64x64 tile in shared memory; 4 threads per r, combined through red[4][64].
+// Tile-vector products on a 64x64 tile in shared memory (pitch 64 + 16
+// bytes), laid out so that each quarter-warp's 16-byte loads hit all 32
+// banks once.
+//
+// mv_rows: out[r] = sum_m T[r][m] v[m].  The quad of lanes 4r..4r+3 owns
+// row r; lane `part` reads the row's 16-byte chunks part + 4u, rotated by
+// three chunks on odd rows (odd rows start 4 banks further on, so the two
+// rows of a quarter-warp then cover distinct banks).  Two shuffles combine
+// the quad; every lane of it returns the row total.
+__device__ __forceinline__ float mv_rows(const float* Tm, const float* v) {
+  constexpr int LD = Pitch<float>::value;
+  const int r = threadIdx.x >> 2, part = threadIdx.x & 3, rot = 3 * (r & 1);
+  float s = 0.f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int ch = (part + 4 * u + rot) & 15;
+    const float4 t = *reinterpret_cast<const float4*>(Tm + r * LD + 4 * ch);
+    const float4 w = *reinterpret_cast<const float4*>(v + 4 * ch);
+    s = fmaf(t.x, w.x, fmaf(t.y, w.y, fmaf(t.z, w.z, fmaf(t.w, w.w, s))));
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+__device__ __forceinline__ double mv_rows(const double* Tm, const double* v) {
+  constexpr int LD = Pitch<double>::value;
+  const int r = threadIdx.x >> 2, part = threadIdx.x & 3, rot = 3 * (r & 1);
+  double s = 0.0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {  // 32 chunks of two doubles per row
+    const int ch = (part + 4 * u + rot) & 31;
+    const double2 t = *reinterpret_cast<const double2*>(Tm + r * LD + 2 * ch);
+    const double2 w = *reinterpret_cast<const double2*>(v + 2 * ch);
+    s = fma(t.x, w.x, fma(t.y, w.y, s));
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
+// mv_cols: out[c] = sum_m T[m][c] v[m] for the columns c = 4g..4g+3 of lane
+// group g = tid / 16.  Lane mr of the group takes rows m = mr + 16k: a
+// quarter-warp reads eight consecutive rows (4 banks apart) at one column
+// offset.  Four butterfly rounds combine the group; every lane of it
+// returns the four totals.
 template <typename R>
-__device__ __forceinline__ R tile_matvec(const R* Tm, const R* v, R* red, int trans) {
+__device__ __forceinline__ void mv_cols(const R* Tm, const R* v, R (&o)[4]) {
   constexpr int LD = Pitch<R>::value;
-  int r = threadIdx.x & 63, part = threadIdx.x >> 6;
-  R s = 0;
-#pragma unroll 4
-  for (int m = 16 * part; m < 16 * part + 16; ++m)
-    s += (trans ? Tm[m * LD + r] : Tm[r * LD + m]) * v[m];
-  red[part * kNB + r] = s;
-  __syncthreads();
-  R tot = red[r] + red[kNB + r] + red[2 * kNB + r] + red[3 * kNB + r];
-  __syncthreads();
-  return tot;
+  const int g = threadIdx.x >> 4, mr = threadIdx.x & 15;
+  R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int m = mr + 16 * k;
+    const R* t = Tm + m * LD + 4 * g;
+    const R w = v[m];
+    if constexpr (sizeof(R) == 4) {
+      const float4 q = *reinterpret_cast<const float4*>(t);
+      a0 = fma((R)q.x, w, a0), a1 = fma((R)q.y, w, a1), a2 = fma((R)q.z, w, a2), a3 = fma((R)q.w, w, a3);
+    } else {
+      const double2 q0 = *reinterpret_cast<const double2*>(t);
+      const double2 q1 = *reinterpret_cast<const double2*>(t + 2);
+      a0 = fma((R)q0.x, w, a0), a1 = fma((R)q0.y, w, a1), a2 = fma((R)q1.x, w, a2), a3 = fma((R)q1.y, w, a3);
+    }
+  }
+#pragma unroll
+  for (int d = 1; d < 16; d <<= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, d);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, d);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, d);
+    a3 += __shfl_xor_sync(0xffffffffu, a3, d);
+  }
+  o[0] = a0, o[1] = a1, o[2] = a2, o[3] = a3;
+}
+
+// Solved blocks of the substitution travel through global memory as tagged
+// 64-bit words: (tag << 32) | 32 bits of the value, one word per float, two
+// (high and low half) per double.  A word is written and read in one piece,
+// so a reader that sees the tag of its launch and phase holds the value
+// itself: no separate flag, no fence, one L2 round trip.  Tags are nonzero
+// and unique per launch and phase, and the buffer is zeroed when a solve
+// sequence starts, so neither stale words nor untouched memory can match.
+__device__ __forceinline__ void put_tagged(uint64_t* w, float v, uint32_t tag) {
+  __stcg(reinterpret_cast<unsigned long long*>(w), ((unsigned long long)tag << 32) | __float_as_uint(v));
+}
+__device__ __forceinline__ void put_tagged(uint64_t* w, double v, uint32_t tag) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  __stcg(reinterpret_cast<unsigned long long*>(w), ((unsigned long long)tag << 32) | (b >> 32));
+  __stcg(reinterpret_cast<unsigned long long*>(w) + 1, ((unsigned long long)tag << 32) | (b & 0xffffffffull));
+}
+__device__ __forceinline__ unsigned long long ld_word(const uint64_t* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+// Waits (bounded) for the word(s) of one value carrying `tag`.
+template <typename R>
+__device__ bool get_tagged(const uint64_t* w, uint32_t tag, R& v, uint32_t* status) {
+  constexpr int NW = sizeof(R) / 4;
+  for (long it = 0; it < kSpinLimit; ++it) {
+    const unsigned long long w0 = ld_word(w);
+    const unsigned long long w1 = NW == 2 ? ld_word(w + 1) : w0;
+    if ((uint32_t)(w0 >> 32) == tag && (uint32_t)(w1 >> 32) == tag) {
+      if constexpr (NW == 1) v = (R)__uint_as_float((uint32_t)w0);
+      else v = (R)__longlong_as_double((long long)((w0 << 32) | (w1 & 0xffffffffull)));
+      return true;
+    }
+    if ((it & 63) == 63 && (ld_status(status) & SC_STATUS_TIMEOUT)) return false;
+    if (it >= 32) __nanosleep(64);
+  }
+  atomicOr(status, SC_STATUS_TIMEOUT);
+  return false;
 }
 
 // Block substitution, one task per tile row: FWD(i) y_i = Linv_ii (b_i -
 // sum_{j<i} L_ij y_j), BWD(i) x_i = Linv_ii^T (y_i - sum_{j>i} L_ji^T x_j).
 // A task streams its tiles through two shared buffers: the copy of the next
-// tile is in flight while it waits for the current dependency.
+// tile is in flight while it waits for the current block of the solution.
+// y_i and then x_i occupy the tagged words of row i (BWD(i) runs after
+// every FWD task has finished, so no reader of y_i remains when x_i
+// replaces it).
 template <typename R>
 __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict__ A, int lda, int nT,
                                                             const R* __restrict__ Linv,
                                                             int n_tasks, int* sync,
                                                             const double* __restrict__ b,
-                                                            R* __restrict__ yw, double* __restrict__ x,
-                                                            int accumulate, uint32_t* status,
-                                                            const LMState* lm) {
+                                                            uint64_t* __restrict__ yw, double* __restrict__ x,
+                                                            int accumulate, uint32_t tag_fwd,
+                                                            uint32_t* status, const LMState* lm) {
   if (lm != nullptr && (lm->done | lm->notpd)) return;
   constexpr int LD = Pitch<R>::value;
+  constexpr int NW = sizeof(R) / 4;  // tagged words per value
+  const uint32_t tag_bwd = tag_fwd + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* buf0 = reinterpret_cast<R*>(smraw);
   R* buf1 = buf0 + kNB * LD;
   R* vin = buf1 + kNB * LD;
-  R* red = vin + kNB;
   __shared__ int s_task, s_ok;
   SyncView sv(sync, nT);
-  int r = threadIdx.x & 63, part = threadIdx.x >> 6;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_task = atomicAdd(sv.sctr, 1);
+    if (threadIdx.x == 0) {
+      s_task = atomicAdd(sv.sctr, 1);
+      s_ok = 1;  // before the barrier: later failure reports cannot be lost
+    }
     __syncthreads();
-    int t = s_task;
+    const int t = s_task;
     if (t >= n_tasks) break;
-    int4 tk = solve_task(nT, t);
-    int i = tk.y;
-    bool fwd = tk.x == T_FWD;
+    const int4 tk = solve_task(nT, t);
+    const int i = tk.y;
+    const bool fwd = tk.x == T_FWD;
     // tile n (0 <= n < cnt) is an off-diagonal tile, tile cnt the inverse
-    int cnt = fwd ? i : nT - 1 - i;
+    const int cnt = fwd ? i : nT - 1 - i;
     auto tile_ptr = [&](int n) -> const R* {
       if (n == cnt) return Linv + (size_t)i * kNB * kNB;
-      int jj = fwd ? n : nT - 1 - n;
+      const int jj = fwd ? n : nT - 1 - n;
       return fwd ? A + (size_t)i * kNB * lda + (size_t)jj * kNB : A + (size_t)jj * kNB * lda + (size_t)i * kNB;
     };
     auto tile_ld = [&](int n) { return n == cnt ? kNB : lda; };
     tile_async(buf0, tile_ptr(0), tile_ld(0));
-    R acc = 0;
+    // forward: quad r = tid / 4 holds acc[r]; backward: lane group g = tid / 16
+    // holds acc[4g..4g+3]
+    R acc[4];
     if (fwd) {
-      acc = (R)b[i * kNB + r];
+      acc[0] = (R)b[i * kNB + (threadIdx.x >> 2)];
     } else {
-      if (threadIdx.x == 0) s_ok = wait_ge(sv.fdone + i, 1, status);
+      R v = 0;
+      if (threadIdx.x < kNB && !get_tagged(yw + (size_t)NW * (i * kNB + threadIdx.x), tag_fwd, v, status))
+        s_ok = 0;
+      if (threadIdx.x < kNB) vin[threadIdx.x] = v;
       __syncthreads();
-      if (!s_ok) break;
-      acc = __ldcg(yw + i * kNB + r);
+      const int g = threadIdx.x >> 4;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] = vin[4 * g + e];
     }
-    bool ok = true;
-    R out = 0;
+    R o[4] = {0, 0, 0, 0};
     for (int n = 0; n <= cnt; ++n) {
       R* cur = (n & 1) ? buf1 : buf0;
       if (n + 1 <= cnt) tile_async((n & 1) ? buf0 : buf1, tile_ptr(n + 1), tile_ld(n + 1));
       else async_commit_empty();
+      __syncthreads();  // every thread is done with vin from the previous tile
       if (n < cnt) {
-        int jj = fwd ? n : nT - 1 - n;
-        if (threadIdx.x == 0) s_ok = wait_ge((fwd ? sv.fdone : sv.bdone) + jj, 1, status);
-        __syncthreads();
-        if (!s_ok) {
-          ok = false;
-          break;
+        const int jj = fwd ? n : nT - 1 - n;
+        if (threadIdx.x < kNB) {
+          R v = 0;
+          if (!get_tagged(yw + (size_t)NW * (jj * kNB + threadIdx.x), fwd ? tag_fwd : tag_bwd, v, status)) s_ok = 0;
+          vin[threadIdx.x] = v;
         }
-        if (threadIdx.x < kNB) vin[threadIdx.x] = __ldcg(yw + jj * kNB + threadIdx.x);
-      } else if (part == 0) {
-        vin[r] = acc;
+      } else if (fwd) {
+        if ((threadIdx.x & 3) == 0) vin[threadIdx.x >> 2] = acc[0];
+      } else if ((threadIdx.x & 15) < 4) {
+        const int e = threadIdx.x & 15;
+        vin[4 * (threadIdx.x >> 4) + e] = e == 0 ? acc[0] : e == 1 ? acc[1] : e == 2 ? acc[2] : acc[3];
       }
       async_wait_prev();
       __syncthreads();
-      R v = tile_matvec(cur, vin, red, fwd ? 0 : 1);
-      if (n < cnt) acc -= v;
-      else out = v;
-    }
-    async_wait_all();
-    if (!ok) break;
-    if (part == 0) {
-      __stcg(yw + i * kNB + r, out);
-      if (!fwd) {
-        double o = (double)out;
-        x[i * kNB + r] = accumulate ? x[i * kNB + r] + o : o;
+      if (!s_ok) break;
+      if (fwd) {
+        const R v = mv_rows(cur, vin);
+        if (n < cnt) acc[0] -= v;
+        else o[0] = v;
+      } else {
+        R v[4];
+        mv_cols(cur, vin, v);
+        if (n < cnt) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[e] -= v[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) o[e] = v[e];
+        }
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      st_release((fwd ? sv.fdone : sv.bdone) + i, 1);
+    async_wait_all();
+    if (!s_ok) break;
+    if (fwd) {
+      if ((threadIdx.x & 3) == 0) put_tagged(yw + (size_t)NW * (i * kNB + (threadIdx.x >> 2)), o[0], tag_fwd);
+    } else if ((threadIdx.x & 15) < 4) {
+      const int e = threadIdx.x & 15, r = 4 * (threadIdx.x >> 4) + e;
+      const R v = e == 0 ? o[0] : e == 1 ? o[1] : e == 2 ? o[2] : o[3];
+      put_tagged(yw + (size_t)NW * (i * kNB + r), v, tag_bwd);
+      x[i * kNB + r] = accumulate ? x[i * kNB + r] + (double)v : (double)v;
     }
   }
   async_wait_all();
 }
 
+static std::atomic<uint32_t> g_solve_launches{0};
+
 template <typename R>
 cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* sync,
-                              const double* b, R* bwork, double* x, int accumulate,
+                              const double* b, uint64_t* bwork, double* x, int accumulate,
                               uint32_t* status, const LMState* lm, cudaStream_t st) {
   int n_tasks = 2 * nT;
-  size_t smem = sizeof(R) * (2 * kNB * Pitch<R>::value + kNB + 4 * kNB);
+  size_t smem = sizeof(R) * (2 * kNB * Pitch<R>::value + kNB);
   static const bool attr_set = [&] {
     cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_chol_solve<R>),
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return true;
   }();
   (void)attr_set;
+  // tags 2e (forward) and 2e + 1 (backward), e >= 1, unique per launch
+  const uint32_t e = (g_solve_launches.fetch_add(1, std::memory_order_relaxed) % 0x7ffffffeu) + 1;
   SyncView sv(sync, nT);
-  // reset the solve counter and the fwd/bwd flags
-  cudaError_t e = cudaMemsetAsync(sv.sctr, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(sv.fdone, 0, sizeof(int) * 2 * nT, st);
-  if (e != cudaSuccess) return e;
-  int grid = std::min(n_tasks, 2 * nT);
-  k_chol_solve<R><<<grid, kCholThreads, smem, st>>>(A, lda, nT, Linv, n_tasks, sync, b, bwork, x,
-                                                    accumulate, status, lm);
+  cudaError_t err = cudaMemsetAsync(sv.sctr, 0, sizeof(int), st);
+  if (err != cudaSuccess) return err;
+  k_chol_solve<R><<<n_tasks, kCholThreads, smem, st>>>(A, lda, nT, Linv, n_tasks, sync, b, bwork, x, accumulate,
+                                                       2 * e, status, lm);
   return cudaGetLastError();
 }
 template cudaError_t launch_chol_solve<float>(const float*, int, int, const float*, int*,
-                                              const double*, float*, double*, int, uint32_t*,
+                                              const double*, uint64_t*, double*, int, uint32_t*,
                                               const LMState*, cudaStream_t);
 template cudaError_t launch_chol_solve<double>(const double*, int, int, const double*, int*,
-                                               const double*, double*, double*, int, uint32_t*,
+                                               const double*, uint64_t*, double*, int, uint32_t*,
                                                const LMState*, cudaStream_t);
 
 }  // namespace sc

@@ -171,7 +171,7 @@ struct Workspace {
   size_t H_cur, H_trial;         // [4N] double
   size_t cpart_cur, cpart_trial; // [N] double
   size_t x, rvec, corr;          // [Ppad] double
-  size_t bvec;                   // [Ppad] real (rhs in the factor's precision)
+  size_t bvec;                   // [Ppad] solved blocks as tagged 64-bit words (1 per float, 2 per double)
   size_t A;          // [Ppad][Ppad] real
   size_t Linv;       // [nT][64][64] real
   size_t sync;       // int: task counters, tile counters, flags
@@ -260,7 +260,7 @@ cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* sta
                         int max_ctas, cudaStream_t st);
 template <typename R>
 cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* sync,
-                              const double* b, R* bwork, double* x, int accumulate,
+                              const double* b, uint64_t* bwork, double* x, int accumulate,
                               uint32_t* status, const LMState* lm, cudaStream_t st);
 
 // lm_control.cu
