@@ -839,6 +839,32 @@ __device__ __forceinline__ void mv_cols(const R* Tm, const R* v, R (&o)[4]) {
   o[0] = a0, o[1] = a1, o[2] = a2, o[3] = a3;
 }
 
+// C = A B for 64x64 tiles in shared memory (all with the tile pitch), 256
+// threads with 4x4 outputs each: A is read as a broadcast per half-warp, B
+// along contiguous rows.
+template <typename R>
+__device__ __forceinline__ void gemm_nn(R* C, const R* A, const R* B) {
+  constexpr int LD = Pitch<R>::value;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  R acc[4][4] = {};
+#pragma unroll 4
+  for (int m = 0; m < kNB; ++m) {
+    R a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = A[(ty + 16 * u) * LD + m];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = B[m * LD + tx + 16 * u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) C[(ty + 16 * u) * LD + tx + 16 * w] = acc[u][w];
+}
+
 // Solved blocks of the substitution travel through global memory as tagged
 // 64-bit words: (tag << 32) | 32 bits of the value, one word per float, two
 // (high and low half) per double.  A word is written and read in one piece,
@@ -880,11 +906,17 @@ __device__ bool get_tagged(const uint64_t* w, uint32_t tag, R& v, uint32_t* stat
 
 // Block substitution, one task per tile row: FWD(i) y_i = Linv_ii (b_i -
 // sum_{j<i} L_ij y_j), BWD(i) x_i = Linv_ii^T (y_i - sum_{j>i} L_ji^T x_j).
-// A task streams its tiles through two shared buffers: the copy of the next
-// tile is in flight while it waits for the current block of the solution.
-// y_i and then x_i occupy the tagged words of row i (BWD(i) runs after
-// every FWD task has finished, so no reader of y_i remains when x_i
-// replaces it).
+// Only the block that arrives last (y_{i-1}, resp. x_{i+1}) lies on the
+// critical path, so a task folds everything else in before it comes:
+//   FWD: M = Linv_ii L_{i,i-1},  z = Linv_ii (b_i - sum_{j<i-1} L_ij y_j),
+//        then y_i = z - M y_{i-1}
+//   BWD: N = L_{i+1,i} Linv_ii,  z = Linv_ii^T (y_i - sum_{j>i+1} L_ji^T x_j),
+//        then x_i = z - N^T x_{i+1}
+// which leaves one tile-vector product between a block's arrival and the
+// publication of the next.  The other tiles stream through two shared
+// buffers while the task waits for their blocks.  y_i and then x_i occupy
+// the tagged words of row i (BWD(i) runs after every FWD task has finished,
+// so no reader of y_i remains when x_i replaces it).
 template <typename R>
 __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict__ A, int lda, int nT,
                                                             const R* __restrict__ Linv,
@@ -898,14 +930,34 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
   constexpr int NW = sizeof(R) / 4;  // tagged words per value
   const uint32_t tag_bwd = tag_fwd + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
-  R* buf0 = reinterpret_cast<R*>(smraw);
-  R* buf1 = buf0 + kNB * LD;
-  R* vin = buf1 + kNB * LD;
+  R* Tinv = reinterpret_cast<R*>(smraw);  // Linv_ii
+  R* Tm = Tinv + kNB * LD;                // M (FWD) or N (BWD)
+  R* B0 = Tm + kNB * LD;                  // the critical tile, then streamed tiles
+  R* B1 = B0 + kNB * LD;
+  R* vin = B1 + kNB * LD;
   __shared__ int s_task, s_ok;
   SyncView sv(sync, nT);
+  const int tid = threadIdx.x;
+  // forward: quad r = tid / 4 owns entry r (acc[0]); backward: lane group
+  // g = tid / 16 owns entries 4g..4g+3
+  auto acc_to_vin = [&](const R (&v)[4], bool fwd) {
+    if (fwd) {
+      if ((tid & 3) == 0) vin[tid >> 2] = v[0];
+    } else if ((tid & 15) < 4) {
+      const int e = tid & 15;
+      vin[4 * (tid >> 4) + e] = e == 0 ? v[0] : e == 1 ? v[1] : e == 2 ? v[2] : v[3];
+    }
+  };
+  auto fetch_block = [&](int row, uint32_t tag) {  // threads < 64: vin <- block `row`
+    if (tid < kNB) {
+      R v = 0;
+      if (!get_tagged(yw + (size_t)NW * (row * kNB + tid), tag, v, status)) s_ok = 0;
+      vin[tid] = v;
+    }
+  };
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       s_task = atomicAdd(sv.sctr, 1);
       s_ok = 1;  // before the barrier: later failure reports cannot be lost
     }
@@ -915,74 +967,83 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
     const int4 tk = solve_task(nT, t);
     const int i = tk.y;
     const bool fwd = tk.x == T_FWD;
-    // tile n (0 <= n < cnt) is an off-diagonal tile, tile cnt the inverse
-    const int cnt = fwd ? i : nT - 1 - i;
-    auto tile_ptr = [&](int n) -> const R* {
-      if (n == cnt) return Linv + (size_t)i * kNB * kNB;
-      const int jj = fwd ? n : nT - 1 - n;
+    const uint32_t tag_in = fwd ? tag_fwd : tag_bwd;  // tag of the blocks of other rows
+    const bool crit = fwd ? i > 0 : i < nT - 1;       // a last-arriving block exists
+    const int jc = fwd ? i - 1 : i + 1;               // ... and its row
+    const int cnt = crit ? (fwd ? i - 1 : nT - 2 - i) : 0;  // the other off-diagonal tiles
+    auto other_row = [&](int n) { return fwd ? n : nT - 1 - n; };
+    auto other_tile = [&](int n) -> const R* {
+      const int jj = other_row(n);
       return fwd ? A + (size_t)i * kNB * lda + (size_t)jj * kNB : A + (size_t)jj * kNB * lda + (size_t)i * kNB;
     };
-    auto tile_ld = [&](int n) { return n == cnt ? kNB : lda; };
-    tile_async(buf0, tile_ptr(0), tile_ld(0));
-    // forward: quad r = tid / 4 holds acc[r]; backward: lane group g = tid / 16
-    // holds acc[4g..4g+3]
-    R acc[4];
+    // group 0: Linv_ii and the critical tile; group 1: the first other tile
+    copy_tile_async(Tinv, Linv + (size_t)i * kNB * kNB, kNB);
+    if (crit)
+      copy_tile_async(B0, fwd ? A + (size_t)i * kNB * lda + (size_t)jc * kNB : A + (size_t)jc * kNB * lda + (size_t)i * kNB,
+                      lda);
+    async_commit();
+    if (cnt > 0) tile_async(B1, other_tile(0), lda);
+    else async_commit_empty();
+    R acc[4] = {0, 0, 0, 0};
     if (fwd) {
-      acc[0] = (R)b[i * kNB + (threadIdx.x >> 2)];
+      acc[0] = (R)b[i * kNB + (tid >> 2)];
     } else {
-      R v = 0;
-      if (threadIdx.x < kNB && !get_tagged(yw + (size_t)NW * (i * kNB + threadIdx.x), tag_fwd, v, status))
-        s_ok = 0;
-      if (threadIdx.x < kNB) vin[threadIdx.x] = v;
+      fetch_block(i, tag_fwd);  // y_i
       __syncthreads();
-      const int g = threadIdx.x >> 4;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[e] = vin[4 * g + e];
+      for (int e = 0; e < 4; ++e) acc[e] = vin[4 * (tid >> 4) + e];
     }
-    R o[4] = {0, 0, 0, 0};
-    for (int n = 0; n <= cnt; ++n) {
-      R* cur = (n & 1) ? buf1 : buf0;
-      if (n + 1 <= cnt) tile_async((n & 1) ? buf0 : buf1, tile_ptr(n + 1), tile_ld(n + 1));
+    async_wait_prev();  // group 0 has landed
+    __syncthreads();
+    if (crit) {
+      if (fwd) gemm_nn(Tm, Tinv, B0);  // M = Linv_ii L_{i,i-1}
+      else gemm_nn(Tm, B0, Tinv);      // N = L_{i+1,i} Linv_ii
+    }
+    for (int n = 0; n < cnt; ++n) {
+      R* cur = (n & 1) ? B0 : B1;
+      __syncthreads();  // every thread is done with vin and with the buffer refilled next
+      if (n + 1 < cnt) tile_async((n & 1) ? B1 : B0, other_tile(n + 1), lda);
       else async_commit_empty();
-      __syncthreads();  // every thread is done with vin from the previous tile
-      if (n < cnt) {
-        const int jj = fwd ? n : nT - 1 - n;
-        if (threadIdx.x < kNB) {
-          R v = 0;
-          if (!get_tagged(yw + (size_t)NW * (jj * kNB + threadIdx.x), fwd ? tag_fwd : tag_bwd, v, status)) s_ok = 0;
-          vin[threadIdx.x] = v;
-        }
-      } else if (fwd) {
-        if ((threadIdx.x & 3) == 0) vin[threadIdx.x >> 2] = acc[0];
-      } else if ((threadIdx.x & 15) < 4) {
-        const int e = threadIdx.x & 15;
-        vin[4 * (threadIdx.x >> 4) + e] = e == 0 ? acc[0] : e == 1 ? acc[1] : e == 2 ? acc[2] : acc[3];
-      }
+      fetch_block(other_row(n), tag_in);
       async_wait_prev();
       __syncthreads();
       if (!s_ok) break;
       if (fwd) {
-        const R v = mv_rows(cur, vin);
-        if (n < cnt) acc[0] -= v;
-        else o[0] = v;
+        acc[0] -= mv_rows(cur, vin);
       } else {
         R v[4];
         mv_cols(cur, vin, v);
-        if (n < cnt) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc[e] -= v[e];
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) o[e] = v[e];
-        }
+        for (int e = 0; e < 4; ++e) acc[e] -= v[e];
       }
     }
     async_wait_all();
     if (!s_ok) break;
+    // z = Linv_ii acc (FWD) or Linv_ii^T acc (BWD)
+    __syncthreads();
+    acc_to_vin(acc, fwd);
+    __syncthreads();
+    R o[4] = {0, 0, 0, 0};
+    if (fwd) o[0] = mv_rows(Tinv, vin);
+    else mv_cols(Tinv, vin, o);
+    if (crit) {  // the critical block: one product
+      __syncthreads();
+      fetch_block(jc, tag_in);
+      __syncthreads();
+      if (!s_ok) break;
+      if (fwd) {
+        o[0] -= mv_rows(Tm, vin);
+      } else {
+        R v[4];
+        mv_cols(Tm, vin, v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o[e] -= v[e];
+      }
+    }
     if (fwd) {
-      if ((threadIdx.x & 3) == 0) put_tagged(yw + (size_t)NW * (i * kNB + (threadIdx.x >> 2)), o[0], tag_fwd);
-    } else if ((threadIdx.x & 15) < 4) {
-      const int e = threadIdx.x & 15, r = 4 * (threadIdx.x >> 4) + e;
+      if ((tid & 3) == 0) put_tagged(yw + (size_t)NW * (i * kNB + (tid >> 2)), o[0], tag_fwd);
+    } else if ((tid & 15) < 4) {
+      const int e = tid & 15, r = 4 * (tid >> 4) + e;
       const R v = e == 0 ? o[0] : e == 1 ? o[1] : e == 2 ? o[2] : o[3];
       put_tagged(yw + (size_t)NW * (i * kNB + r), v, tag_bwd);
       x[i * kNB + r] = accumulate ? x[i * kNB + r] + (double)v : (double)v;
@@ -998,7 +1059,7 @@ cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* s
                               const double* b, uint64_t* bwork, double* x, int accumulate,
                               uint32_t* status, const LMState* lm, cudaStream_t st) {
   int n_tasks = 2 * nT;
-  size_t smem = sizeof(R) * (2 * kNB * Pitch<R>::value + kNB);
+  size_t smem = sizeof(R) * (4 * kNB * Pitch<R>::value + kNB);
   static const bool attr_set = [&] {
     cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_chol_solve<R>),
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
