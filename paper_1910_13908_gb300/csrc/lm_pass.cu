@@ -17,6 +17,8 @@
 // Memory: one thread per (baseline, timeslot chunk); consecutive threads take
 // consecutive baselines, whose [F][2][2] complex blocks are contiguous in the
 // [T][B][F][2][2] layout, so every warp streams contiguous memory.
+#include <algorithm>
+
 #include "sc_common.cuh"
 
 namespace sc {
@@ -29,8 +31,11 @@ __global__ void __launch_bounds__(256) k_pass(int N, int T, int F, int64_t B, in
                                               R* __restrict__ stat_cost, R* __restrict__ stat_rho,
                                               const LMState* __restrict__ lm) {
   if (lm != nullptr && (lm->done | lm->skip)) return;
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nchunk * B) return;
+  const int64_t n_items = (int64_t)nchunk * B;
+  // grid-stride over (chunk, baseline) items: the grid is sized to the
+  // resident blocks, so no partly filled last wave
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_items;
+       idx += (int64_t)gridDim.x * blockDim.x) {
   int chunk = (int)(idx / B);
   int64_t b = idx - (int64_t)chunk * B;
   int p, q;
@@ -41,6 +46,7 @@ __global__ void __launch_bounds__(256) k_pass(int N, int T, int F, int64_t B, in
   R cost = 0;
   m22<R> rho = mzero<R>();
   int t0 = chunk * tchunk, t1 = min(T, t0 + tchunk);
+#pragma unroll 2
   for (int t = t0; t < t1; ++t) {
     size_t v0 = ((size_t)t * B + b) * F;
 #pragma unroll 4
@@ -72,15 +78,25 @@ __global__ void __launch_bounds__(256) k_pass(int N, int T, int F, int64_t B, in
     stat_cost[o] = cost;
     st_vis(stat_rho + 8 * o, rho);
   }
+  }
 }
 
 template <typename R, int FL>
 static cudaError_t go_pass(const Shape& s, const R* Xin, const R* C, const double* J_old,
                            const double* J_cur, R* Rout, R* stat_cost, R* stat_rho, int nchunk,
                            int tchunk, const LMState* lm, cudaStream_t st) {
-  int64_t n = (int64_t)nchunk * s.B;
-  k_pass<R, FL><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s.N, s.T, s.F, s.B, nchunk, tchunk, Xin, C,
-                                                             J_old, J_cur, Rout, stat_cost, stat_rho, lm);
+  // resident blocks of this instantiation, computed once (thread-safe static)
+  static const int resident = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pass<R, FL>, 256, 0);
+    return std::max(1, sms * std::max(per, 1));
+  }();
+  const int64_t n = (int64_t)nchunk * s.B;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, resident);
+  k_pass<R, FL><<<grid, 256, 0, st>>>(s.N, s.T, s.F, s.B, nchunk, tchunk, Xin, C, J_old, J_cur, Rout,
+                                      stat_cost, stat_rho, lm);
   return cudaGetLastError();
 }
 
@@ -126,11 +142,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
-// One block of 4 warps per station s: lanes stride over the other stations
-// o, form the baseline's contribution in float64 and accumulate in float64;
-// shuffles and one shared-memory step combine the 128 partial sums.
+// One block of kReduceThreads threads per station s: lanes stride over the
+// other stations o, form the baseline's contribution in float64 and
+// accumulate in float64; shuffles and one shared-memory step combine the
+// partial sums.  (256 threads per station measured slower than 128.)
+constexpr int kReduceThreads = 128;
 template <typename R>
-__global__ void __launch_bounds__(128) k_station_reduce(int N, int64_t B, int nchunk,
+__global__ void __launch_bounds__(kReduceThreads) k_station_reduce(int N, int64_t B, int nchunk,
                                                         const R* __restrict__ stat_cost,
                                                         const R* __restrict__ stat_rho,
                                                         const R* __restrict__ w,
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(128) k_station_reduce(int N, int64_t B, int nc
                                                         double* __restrict__ cpart,
                                                         const LMState* __restrict__ lm) {
   if (lm != nullptr && (lm->done | lm->skip)) return;
-  __shared__ double part[4][13];
+  __shared__ double part[kReduceThreads / 32][13];
   int s = blockIdx.x;
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc[13];
@@ -179,7 +197,9 @@ __global__ void __launch_bounds__(128) k_station_reduce(int N, int64_t B, int nc
   __syncthreads();
   if (threadIdx.x < 13) {
     int i = threadIdx.x;
-    double t = part[0][i] + part[1][i] + part[2][i] + part[3][i];
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kReduceThreads / 32; ++w) t += part[w][i];
     if (i < 8) g[8 * s + i] = t;
     else if (i < 12) H[4 * s + i - 8] = t;
     else cpart[s] = t;
@@ -190,7 +210,7 @@ template <typename R>
 cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
                                   int nchunk, const R* w, const double* J, double* g, double* H,
                                   double* cpart, const LMState* lm, cudaStream_t st) {
-  k_station_reduce<R><<<s.N, 128, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm);
+  k_station_reduce<R><<<s.N, kReduceThreads, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm);
   return cudaGetLastError();
 }
 template cudaError_t launch_station_reduce<float>(const Shape&, const float*, const float*, int,

@@ -126,10 +126,11 @@ __host__ __device__ __forceinline__ int64_t row_start(int p, int N) {
 __host__ __device__ __forceinline__ int64_t bl_index(int p, int q, int N) {
   return row_start(p, N) + (q - p - 1);
 }
-// inverse of bl_index
+// inverse of bl_index: a float32 estimate from the quadratic formula (FP32
+// is 64x the FP64 rate here), made exact by the integer comparisons below
 __device__ __forceinline__ void bl_pair(int64_t b, int N, int& p, int& q) {
-  double n2 = 2.0 * N - 1.0;
-  int pp = (int)floor(0.5 * (n2 - sqrt(fmax(n2 * n2 - 8.0 * (double)b, 0.0))));
+  const float n2 = 2.0f * N - 1.0f;
+  int pp = (int)floorf(0.5f * (n2 - sqrtf(fmaxf(n2 * n2 - 8.0f * (float)b, 0.0f))));
   if (pp < 0) pp = 0;
   if (pp > N - 2) pp = N - 2;
   while (pp > 0 && row_start(pp, N) > b) --pp;
