@@ -254,3 +254,42 @@ def test_full_size_precision_path_matches_fp64_path():
     np.testing.assert_allclose(c32, c64, rtol=1e-4)
     for k in range(spec.K):
         assert O.aligned_error(J32[k], J64[k]) <= 1e-4
+
+
+def test_full_size_512_station_cluster_mixed_matches_fp64():
+    """One cluster of the 512-station workload (130816 baselines, 10
+    timeslots, 4 channels, 100 sources): the mixed path factorises and solves
+    at order 4096, as the bench does, and its final cost and Jones after 10 LM
+    steps agree with the plain FP64 GPU path (itself pinned to the oracle
+    above); the cost falls well below its starting value."""
+    import dataclasses
+    spec = dataclasses.replace(synth.config("c4"), K=1)
+    uvw, f, sky = synth.station_uvw(spec), synth.freqs(spec), synth.sky(spec)
+    Jt = synth.jones_true(spec)
+    shp = sc.Shape(spec.N, spec.T, spec.F, spec.K, spec.S)
+    dsky = sc.DeviceSky.from_synth(sky)
+    u, fr = tdev(uvw, torch.float64), tdev(f, torch.float64)
+    ws64 = sc.workspace(shp, sc.SC_FP64)
+    C = sc.predict_coherencies(shp, u, fr, dsky, sc.SC_FP64, ws64)
+    Jtd = tdev(Jt, torch.complex128)
+    p, q = np.triu_indices(spec.N, 1)
+    G = Jtd[:, p] @ Jtd[:, q].conj().transpose(-1, -2)                     # [1][B][2][2]
+    V = torch.einsum("ktbf,kbij->tbfij", C, G) + tdev(synth.noise(spec), torch.complex128)
+    del C, G
+    res = {}
+    for prec in PRECS:
+        ws = ws64 if prec == sc.SC_FP64 else sc.workspace(shp, prec)
+        Jg = tdev(synth.identity_jones(spec.K, spec.N), torch.complex128)
+        Cp = sc.predict_coherencies(shp, u, fr, dsky, prec, ws)
+        _, cost0 = sc.residual(shp, V.to(cdt(prec)).contiguous(), Cp[0].contiguous(), Jg[0], prec, ws)
+        _, cost, iters = sc.solve_cluster(shp, V.to(cdt(prec)).contiguous(), Cp[0].contiguous(), Jg[0], prec, ws,
+                                          n_lm=10, refine_sweeps=1, eps_grad=0.0)
+        assert sc.device_status(ws) == 0
+        res[prec] = (float(cost0), cost.item(), Jg[0].cpu().numpy(), iters.item())
+        del Cp
+    c0, c64, J64, it64 = res[sc.SC_FP64]
+    _, c32, J32, it32 = res[sc.SC_MIXED]
+    assert it64 == it32 == 10
+    assert c64 < 0.5 * c0
+    assert abs(c32 - c64) <= 1e-4 * c64
+    assert O.aligned_error(J32, J64) <= 1e-4
