@@ -11,17 +11,18 @@
 //   FWD(i)        y_i = Linv_ii (b_i - sum_{j<i} L_ij y_j)
 //   BWD(i)        x_i = Linv_ii^T (y_i - sum_{j>i} L_ji^T x_j)
 // CTAs take tasks in list order (one atomic counter; the list is decoded,
-// not stored)
-// and wait, with a bounded spin, for the counters of the tiles they read.
-// Every dependency of a task lies earlier in the list, so the earliest
-// unfinished task can always run and the graph cannot deadlock; the list
-// puts the next panel's POTRF/TRSM right after the updates they need
-// (look-ahead of one panel), so the factorisation's critical path overlaps
-// the bulk of the trailing updates.
+// not stored) and wait, with a bounded spin, for the counters of the tiles
+// they read.  Every dependency of a task lies earlier in the list, so the
+// earliest unfinished task can always run and the graph cannot deadlock; the
+// list puts the next panel's POTRF/TRSM right after the updates they need
+// (look-ahead of one panel), and one CTA (the walker) runs the diagonal
+// chain POTRF -> TRSM -> UPDATE itself, so the critical path overlaps the
+// bulk of the trailing updates.  The solves take their tasks the same way
+// but wait on the solved blocks themselves (tagged words, below).
 //
 // Tiles written by one SM and read by another are moved through L2 only
-// (ld.global.cg / st.global.cg), and published with a fence followed by a
-// release store of the tile's counter.
+// (ld.global.cg / st.global.cg) and published by a release store of the
+// tile's counter, made after the block barrier that follows the stores.
 #include <algorithm>
 #include <atomic>
 #include <type_traits>
@@ -32,26 +33,24 @@ namespace sc {
 
 enum TaskType { T_POTRF = 0, T_TRSM = 1, T_UPD = 2, T_FWD = 3, T_BWD = 4 };
 
-// sync area (ints): [0] factor task counter, [1] solve task counter,
-// upd[nT*nT], potrf_done[nT], trsm_done[nT*nT], fwd_done[nT], bwd_done[nT]
+// sync area (ints): [0] factor task counter, [1] solve task counter (and,
+// during a factorisation, the walker's SM + 1), upd[nT*nT], potrf_done[nT],
+// trsm_done[nT*nT].  The solves pass their blocks as tagged words instead.
 struct SyncView {
   int* fctr;
   int* sctr;
   int* upd;
   int* pdone;
   int* tdone;
-  int* fdone;
-  int* bdone;
   __host__ __device__ SyncView(int* s, int nT)
-      : fctr(s), sctr(s + 1), upd(s + 2), pdone(s + 2 + nT * nT), tdone(s + 2 + nT * nT + nT),
-        fdone(s + 2 + 2 * nT * nT + nT), bdone(s + 2 + 2 * nT * nT + 2 * nT) {}
+      : fctr(s), sctr(s + 1), upd(s + 2), pdone(s + 2 + nT * nT), tdone(s + 2 + nT * nT + nT) {}
 };
 
-int chol_sync_ints(int nT) { return 2 + 2 * nT * nT + 3 * nT; }
-// ints from the start of the sync area that a factorisation resets
-static int chol_factor_reset_ints(int nT) { return 2 + 2 * nT * nT + nT; }
+int chol_sync_ints(int nT) { return 2 + 2 * nT * nT + nT; }
+// a factorisation resets the whole sync area
+static int chol_factor_reset_ints(int nT) { return chol_sync_ints(nT); }
 
-// Task t of the factorisation list (decoded in O(nT), no list in memory):
+// Task t of the factorisation list (decoded, no list in memory):
 //   POTRF(0), TRSM(1..nT-1, 0), then for each panel j = 0..nT-2:
 //   UPDATE(j+1..nT-1, j+1, j)   -- the next panel column first
 //   POTRF(j+1), TRSM(j+2..nT-1, j+1)
