@@ -584,8 +584,8 @@ __device__ __forceinline__ void task_operands_async(int4 tk, const R* A, int lda
   async_commit();
 }
 
-// Persistent tile-DAG factorisation.  Block 0's first claim is task 0: it
-// becomes the walker.  Every other block runs TRSM and UPDATE tasks in
+// Persistent tile-DAG factorisation.  The block that claims task 0 becomes
+// the walker.  Every other block runs TRSM and UPDATE tasks in
 // list order, two deep: while it multiplies the current task, the operands
 // of the task it claimed next are already on their way into the other
 // buffer pair, provided that task's dependencies were complete when it
