@@ -47,6 +47,12 @@ What pins each function (tests/test_oracle.py):
   minimum; a multistart search on 3 stations finds no lower cost.
 * sage_calibrate: K = 1 is the single-cluster LM bit for bit; noiseless
   multi-cluster recovery; the total cost never increases over EM sweeps.
+* residual_all: against visibilities built one at a time with explicit 2x2
+  products, removing every cluster leaves exactly the planted unmodelled
+  signal A, and one cluster left in leaves its model; A seen through the gains
+  of direction c comes back as A after correcting for c (each c); identity
+  gains correct nothing; rank-one and zero Jones are flagged and zeroed;
+  the unitary ambiguity turns the corrected residual into U^H R U.
 """
 from __future__ import annotations
 
@@ -133,6 +139,53 @@ def residual(X, C, J):
     """R = X - J_p C J_q^H and cost = sum |R|^2 (squared Frobenius norms)."""
     R = X - model_vis(C, J)
     return R, float(np.sum(R.real ** 2 + R.imag ** 2))
+
+
+# Threshold of the singular-Jones test of residual_all: a station's Jones J
+# counts as singular when |det J| <= SINGULAR_RTOL * |J|_F^2 (|det J| is at
+# most |J|_F^2 / 2, with equality for a multiple of a unitary matrix).
+SINGULAR_RTOL = 1e-12
+
+
+def residual_all(V, Cs, J, corr=-1):
+    """Residual of the whole sky model after calibration, optionally corrected
+    for the gains of one direction (the output that follows the solve: data
+    with every calibrated cluster removed, left for imaging).
+
+        R_pq = V_pq - sum_k J_kp (C_kpq Id) J_kq^H
+        cost = sum |R|^2                      (before any correction)
+        if corr >= 0:  R_pq <- J_cp^{-1} R_pq J_cq^{-H},  c = corr
+
+    Inputs: V [T][B][F][2][2], Cs [K][T][B][F], J [K][N][2][2].  A station
+    whose J_c is singular (SINGULAR_RTOL) cannot be corrected: every
+    visibility of its baselines is set to zero.  The 2x2 inverse is the
+    adjugate over the determinant.  Returns (R, cost, singular [N] bool).
+    """
+    K, N = J.shape[0], J.shape[1]
+    p, q = baselines(N)
+    R = np.array(V, dtype=np.complex128)
+    for k in range(K):
+        R = R - model_vis(Cs[k], J[k])
+    cost = float(np.sum(R.real ** 2 + R.imag ** 2))
+    singular = np.zeros(N, dtype=bool)
+    if corr < 0:
+        return R, cost, singular
+    Jinv = np.zeros((N, 2, 2), dtype=np.complex128)
+    for s in range(N):
+        a, b = J[corr, s, 0, 0], J[corr, s, 0, 1]
+        c, d = J[corr, s, 1, 0], J[corr, s, 1, 1]
+        det = a * d - b * c
+        fro2 = abs(a) ** 2 + abs(b) ** 2 + abs(c) ** 2 + abs(d) ** 2
+        if abs(det) <= SINGULAR_RTOL * fro2:
+            singular[s] = True
+            continue
+        Jinv[s] = np.array([[d, -b], [-c, a]]) / det
+    # J_cp^{-1} R J_cq^{-H}; a singular station has Jinv = 0, so its
+    # baselines come out zero
+    Lp = Jinv[p][None, :, None, :, :]
+    Rq = np.conj(np.swapaxes(Jinv[q], -1, -2))[None, :, None, :, :]
+    R = Lp @ R @ Rq
+    return R, cost, singular
 
 
 def simulate(uvw, freqs, sky, J_true, noise=None):

@@ -306,3 +306,95 @@ def test_procrustes_recovers_a_known_rotation():
     J = Jt @ U.conj().T
     np.testing.assert_allclose(O.align_unitary(J, Jt), U, atol=1e-12)
     assert O.aligned_error(J, Jt) < 1e-12
+
+
+# --- residual of all clusters and its correction ---------------------------------
+
+def _brute_vis(Cs, J, A=None, c=None):
+    """V_pq = sum_k J_kp (C_kpq Id) J_kq^H (+ J_cp A_pq J_cq^H), one visibility
+    at a time, with explicit 2x2 products."""
+    K, T, B, F = Cs.shape
+    N = J.shape[1]
+    pq = [(a, b) for a in range(N) for b in range(a + 1, N)]
+    V = np.zeros((T, B, F, 2, 2), dtype=np.complex128)
+    for t in range(T):
+        for b, (p, q) in enumerate(pq):
+            for f in range(F):
+                for k in range(K):
+                    V[t, b, f] += J[k, p] @ (Cs[k, t, b, f] * np.eye(2)) @ J[k, q].conj().T
+                if A is not None:
+                    V[t, b, f] += J[c, p] @ A[t, b, f] @ J[c, q].conj().T
+    return V
+
+
+def test_residual_all_removes_every_cluster():
+    spec = small_spec(N=5, T=2, F=2, K=3, S=3, seed=21, sigma=0.3)
+    Cs, Jt = _multi(spec)
+    A = synth.noise(spec)
+    V = _brute_vis(Cs, Jt) + A
+    R, cost, sing = O.residual_all(V, Cs, Jt)
+    np.testing.assert_allclose(R, A, rtol=0, atol=1e-12 * np.abs(V).max())
+    assert math.isclose(cost, float(np.sum(np.abs(A) ** 2)), rel_tol=1e-9)
+    assert not sing.any()
+    # leaving one cluster in the data leaves exactly its model behind
+    R2, _, _ = O.residual_all(V, Cs[:2], Jt[:2])
+    np.testing.assert_allclose(R2 - A, _brute_vis(Cs[2:], Jt[2:]), rtol=0,
+                               atol=1e-12 * np.abs(V).max())
+
+
+def test_residual_all_correction_recovers_the_planted_signal():
+    # the unmodelled signal A seen through direction c's gains comes back as A
+    spec = small_spec(N=6, T=2, F=3, K=3, S=2, seed=22, sigma=0.5, jones_var=0.3)
+    Cs, Jt = _multi(spec)
+    A = synth.noise(spec)
+    for c in range(3):
+        V = _brute_vis(Cs, Jt, A, c)
+        R, cost, sing = O.residual_all(V, Cs, Jt, corr=c)
+        np.testing.assert_allclose(R, A, rtol=0, atol=1e-11 * np.abs(A).max())
+        seen = _brute_vis(np.zeros_like(Cs[:1]), Jt[c:c + 1], A, 0)
+        assert math.isclose(cost, float(np.sum(np.abs(seen) ** 2)), rel_tol=1e-9)
+        assert not sing.any()
+
+
+def test_residual_all_identity_gains_correct_nothing():
+    spec = small_spec(N=5, T=2, F=2, K=2, S=2, seed=23)
+    Cs, Jt = _multi(spec)
+    V = _brute_vis(Cs, Jt) + synth.noise(spec)
+    J = Jt.copy()
+    J[1] = np.eye(2)
+    R0, c0, _ = O.residual_all(V, Cs, J)
+    R1, c1, _ = O.residual_all(V, Cs, J, corr=1)
+    assert np.array_equal(R0, R1) and c0 == c1
+
+
+def test_residual_all_singular_stations_are_zeroed():
+    spec = small_spec(N=6, T=2, F=2, K=2, S=2, seed=24, sigma=0.5)
+    Cs, Jt = _multi(spec)
+    J = Jt.copy()
+    J[0, 1] = [[1.0, 2.0j], [0.5, 1.0j]]          # rank one: det = 0
+    J[0, 4] = 0.0
+    A = synth.noise(spec)
+    V = _brute_vis(Cs, J, A, 0)
+    R, _, sing = O.residual_all(V, Cs, J, corr=0)
+    assert sing.tolist() == [False, True, False, False, True, False]
+    p, q = synth.baseline_pairs(spec.N)
+    hit = sing[p] | sing[q]
+    assert np.all(R[:, hit] == 0)
+    np.testing.assert_allclose(R[:, ~hit], A[:, ~hit], rtol=0, atol=1e-11 * np.abs(A).max())
+
+
+def test_residual_all_is_invariant_to_the_unitary_ambiguity():
+    # J_k -> J_k U_k leaves every model unchanged; the corrected residual turns
+    # into U_c^H R U_c, so its per-visibility Frobenius norms stay the same
+    spec = small_spec(N=5, T=2, F=2, K=2, S=2, seed=25, sigma=0.2)
+    Cs, Jt = _multi(spec)
+    V = _brute_vis(Cs, Jt) + synth.noise(spec)
+    H = np.array([[0.7, 0.1 + 0.4j], [0.1 - 0.4j, -0.2]])
+    w, v = np.linalg.eigh(H)
+    U = v @ np.diag(np.exp(1j * w)) @ v.conj().T
+    R0, c0, _ = O.residual_all(V, Cs, Jt, corr=1)
+    R1, c1, _ = O.residual_all(V, Cs, Jt @ U, corr=1)
+    assert math.isclose(c0, c1, rel_tol=1e-12)
+    np.testing.assert_allclose(R1, U.conj().T @ R0 @ U, rtol=0, atol=1e-12 * np.abs(R0).max())
+    np.testing.assert_allclose(np.linalg.norm(R1, axis=(-2, -1)), np.linalg.norm(R0, axis=(-2, -1)),
+                               rtol=1e-12, atol=1e-14)
