@@ -230,6 +230,43 @@ def roofline_for(kind, spec, prec, n_em, n_lm, launches, ms, pk, peak_src):
     return dict(bound="latency", achieved=None, peak=None, unit=None)
 
 
+def measure_residual_output(job, spec, prec, J, reps, pk, src, workload):
+    """The output that follows calibration: the residual of all K clusters
+    with the calibrated Jones, corrected towards cluster 0 (sc_residual_all),
+    timed on its own after the calibration steps.  HBM-bound: per visibility
+    it reads V and the K coherencies and writes R once."""
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    C = sc.predict_coherencies(job["shape"], job["uvw"], job["freqs"], job["sky"], prec, job["ws"])
+    R = torch.empty_like(job["V"])
+    for _ in range(2):
+        sc.residual_all(job["shape"], job["V"], C, J, prec, job["ws"], corr=0, out=R)
+    torch.cuda.synchronize()
+    sc.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        _, cost = sc.residual_all(job["shape"], job["V"], C, J, prec, job["ws"], corr=0, out=R)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = sc.profile_end()
+    status = sc.device_status(job["ws"])
+    n, kms = prof["vis_pass"]
+    rs = 4 if prec == sc.SC_MIXED else 8
+    vis = spec.B * spec.T * spec.F
+    work = vis * (8 * rs + 2 * rs * spec.K + 8 * rs)     # read V, read C of every cluster, write R
+    avg_s = kms / 1e3 / max(n, 1)
+    achieved = work / avg_s / 1e9
+    del C, R
+    return {"call": "sc_residual_all", "corr": 0, "launches": n,
+            "avg_launch_us": round(avg_s * 1e6, 2), "call_ms": round(e0.elapsed_time(e1) / reps, 4),
+            "vis_per_s": vis / avg_s, "bytes_per_launch": int(work),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": NCU_TRAFFIC.get(("residual_all", workload)),
+                         "peak_kind": src},
+            "cost": float(cost.item()), "device_status": status}
+
+
 # DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/),
 # keyed by (kernel kind, workload); None until captured for the current kernel.
 NCU_TRAFFIC = {}
@@ -330,6 +367,9 @@ def run_ours(args, rank, world, local_rank):
         fp64 = compare_fp64(spec, dev, args)
 
     pk, src = peaks()
+    resid = None
+    if not args.no_residual:
+        resid = measure_residual_output(job, spec, prec, J, 5, pk, src, args.workload)
     dominant = max(prof, key=lambda k: prof[k][1])
     n_dom, ms_dom = prof[dominant]
     roof = roofline_for(dominant, spec, prec, n_em, n_lm, n_dom, ms_dom, pk, src)
@@ -368,6 +408,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(n_launch),
         "clocks": clk,
         "fp64_gpu": fp64,
+        "residual_output": resid,
         "kernel_ms": breakdown,
         "final_costs_head": final_costs[:4],
     }
@@ -604,6 +645,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-residual", action="store_true",
+                    help="skip the timed residual output (sc_residual_all) after the steps")
     ap.add_argument("--jobs", type=int, default=0, help="jobs of the batch64 (64) / serve500 (500) workloads")
     ap.add_argument("--slots", type=int, default=8, help="concurrent jobs of the serving workload")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (Hz); 0 = 0.8 x capacity")

@@ -84,6 +84,9 @@ extern "C" {
 /* Device status bits (sc_device_status) */
 #define SC_STATUS_NOTPD 1u
 #define SC_STATUS_TIMEOUT 2u
+#define SC_STATUS_SINGULAR 4u /* sc_residual_all: a Jones of the correction
+                                 direction was singular; its baselines were
+                                 zeroed */
 
 typedef enum sc_precision {
   SC_FP64 = 0,  /* everything in float64 / complex128 */
@@ -223,6 +226,37 @@ SC_API int32_t sc_residual_noalloc(const sc_dims* d, const void* X, const void* 
                                    const double* jones, void* R, double* cost,
                                    int32_t prec, void* stream, char* errbuf,
                                    size_t errlen);
+
+/* After calibration: the residual of the whole sky model, optionally
+ * corrected for the gains of one direction.  This is the data handed on to
+ * imaging once every calibrated cluster has been removed (the abstract
+ * states the aim: calibration with minimum artefacts from an incomplete sky
+ * model; what remains is the part of the sky the model lacks).
+ *   R = V - sum_k J_kp (C_kpq Id) J_kq^H        over all K = d->K clusters
+ *   if corr >= 0:  R <- J_cp^{-1} R J_cq^{-H},  c = corr
+ * Arguments:
+ *   V     DEVICE [T][B][F][2][2] complex observed visibilities
+ *   C     DEVICE [K][T][B][F] complex coherencies of every cluster, as
+ *         written by sc_predict_coherencies
+ *   jones DEVICE complex128 [K][N][2][2], e.g. the output of
+ *         sc_calibrate_sage
+ *   corr  cluster whose inverse gains are applied, in [0, K); -1 for none
+ *   R     DEVICE out, same layout as V; may equal V (in place), must not
+ *         otherwise overlap V or C
+ *   cost  DEVICE out float64 scalar, sum |R|_F^2 before the correction (the
+ *         calibration's total cost); may be NULL
+ * Complex types as everywhere: complex64 for SC_MIXED, complex128 for
+ * SC_FP64.  In SC_MIXED the Jones are rounded to float32 and the sum is
+ * formed in float32; the inverses are formed in float64 and then rounded.
+ * A station whose Jones of cluster corr has |det J| <= 1e-12 |J|_F^2 has no
+ * usable inverse: the visibilities of all its baselines are set to zero and
+ * the device status gets SC_STATUS_SINGULAR (the call still returns SC_OK).
+ * Errors: SC_EINVAL (NULL V, C, jones or R; corr outside [-1, K); bad
+ * shape), SC_ENOMEM (workspace too small), SC_ECUDA. */
+SC_API int32_t sc_residual_all(const sc_dims* d, const void* V, const void* C,
+                               const double* jones, int32_t corr, void* R,
+                               double* cost, int32_t prec, void* ws,
+                               size_t ws_bytes, void* stream);
 
 /* Step (c): Gauss-Newton normal equations of one cluster at residual R
  * (= X - model at `jones`):

@@ -99,6 +99,9 @@ Workspace plan_workspace(const Shape& s, bool job) {
   L.A = take((size_t)L.Ppad * L.Ppad * rs);
   L.Linv = take((size_t)L.nT * kNB * kNB * rs);
   L.sync = take((size_t)chol_sync_ints(L.nT) * 4);
+  L.gains = take(K * N * 8 * rs);
+  L.gain_inv = take(N * 8 * rs);
+  L.parts = take((size_t)kMaxParts * 8);
   L.total = o;
   return L;
 }
@@ -315,6 +318,22 @@ static int residual_impl(const Ctx& c, const void* X, const void* C, const doubl
 }
 
 template <typename R>
+static int residual_all_impl(const Ctx& c, const void* V, const void* C, const double* jones, int corr,
+                             void* Rout, double* cost) {
+  const Workspace& L = c.L;
+  R* Jr = c.at<R>(L.gains);
+  R* Jinv = c.at<R>(L.gain_inv);
+  double* part = cost ? c.at<double>(L.parts) : nullptr;
+  int n_parts = 0;
+  SC_LAUNCH(PK_OTHER, launch_gain_prep<R>(c.s, jones, corr, Jr, Jinv, c.status(), c.st));
+  SC_LAUNCH(PK_PASS, launch_residual_all<R>(c.s, static_cast<const R*>(V), static_cast<const R*>(C), Jr,
+                                            corr >= 0 ? Jinv : nullptr, static_cast<R*>(Rout), part,
+                                            kMaxParts, &n_parts, c.st));
+  if (cost) SC_LAUNCH(PK_OTHER, launch_sum_cost(part, n_parts, cost, c.st));
+  return SC_OK;
+}
+
+template <typename R>
 static int normal_eqs_impl(const Ctx& c, const void* Rv, const void* C, const double* jones, void* JhJ,
                            double* Jhr) {
   const Workspace& L = c.L;
@@ -425,6 +444,21 @@ SC_API int32_t sc_residual(const sc_dims* d, const void* X, const void* C, const
   if (!X || !C || !jones) return fail(SC_EINVAL, "X, C and jones must not be NULL");
   r = prec == SC_MIXED ? residual_impl<float>(c, X, C, jones, R, cost)
                        : residual_impl<double>(c, X, C, jones, R, cost);
+  return r ? r : ok();
+}
+
+SC_API int32_t sc_residual_all(const sc_dims* d, const void* V, const void* C, const double* jones,
+                               int32_t corr, void* R, double* cost, int32_t prec, void* ws,
+                               size_t ws_bytes, void* stream) {
+  Ctx c;
+  // argument checks first: they touch no device memory
+  int r = check_dims(d, prec, c.s);
+  if (r) return r;
+  if (!V || !C || !jones || !R) return fail(SC_EINVAL, "V, C, jones and R must not be NULL");
+  if (corr < -1 || corr >= c.s.K) return fail(SC_EINVAL, "corr = %d outside [-1, K = %d)", corr, c.s.K);
+  if ((r = open_ctx(c, d, prec, ws, ws_bytes, stream))) return r;
+  r = prec == SC_MIXED ? residual_all_impl<float>(c, V, C, jones, corr, R, cost)
+                       : residual_all_impl<double>(c, V, C, jones, corr, R, cost);
   return r ? r : ok();
 }
 

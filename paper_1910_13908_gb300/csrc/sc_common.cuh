@@ -12,6 +12,7 @@ namespace sc {
 constexpr double kCLight = 299792458.0;
 constexpr int kNB = 64;          // Cholesky tile edge
 constexpr int kCholThreads = 256;
+constexpr int kMaxParts = 4096;  // per-block partial sums of sc_residual_all
 
 // ---- complex scalars -----------------------------------------------------------
 
@@ -176,6 +177,10 @@ struct Workspace {
   size_t A;          // [Ppad][Ppad] real
   size_t Linv;       // [nT][64][64] real
   size_t sync;       // int: task counters, tile counters, flags
+  // residual of all clusters (sc_residual_all)
+  size_t gains;      // [K][N][8] real, every cluster's Jones rounded to the data type
+  size_t gain_inv;   // [N][8] real, inverse Jones of the correction direction
+  size_t parts;      // [kMaxParts] double, per-block cost sums
   int nT, Ppad, nchunk, tchunk, splits;
 };
 
@@ -240,6 +245,17 @@ cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* s
 cudaError_t launch_sum_cost(const double* cpart, int N, double* out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sum_reals(const R* x, int64_t n, double* out, cudaStream_t st);
+
+// residual_all.cu
+template <typename R>
+cudaError_t launch_gain_prep(const Shape& s, const double* J, int corr, R* Jr, R* Jinv,
+                             uint32_t* status, cudaStream_t st);
+// Jinv = NULL: no correction; part = NULL: no cost partial sums.  Writes the
+// number of partial sums (the grid) to *n_parts; at most max_parts.
+template <typename R>
+cudaError_t launch_residual_all(const Shape& s, const R* V, const R* C, const R* Jr,
+                                const R* Jinv, R* Rout, double* part, int max_parts, int* n_parts,
+                                cudaStream_t st);
 
 // normal_eqs.cu
 template <typename R>

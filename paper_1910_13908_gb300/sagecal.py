@@ -24,6 +24,11 @@ from . import build as _build
 SC_FP64 = 0
 SC_MIXED = 1
 
+# device status bits (sc_device_status)
+SC_STATUS_NOTPD = 1
+SC_STATUS_TIMEOUT = 2
+SC_STATUS_SINGULAR = 4
+
 _c = ctypes
 _LIB = None
 
@@ -76,6 +81,7 @@ def lib():
         L.sc_chol_schedule.argtypes = [i32, i32, _c.POINTER(i32), i32]
         L.sc_predict_coherencies.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, i32, vp, sz, vp]
         L.sc_residual.argtypes = [D, vp, vp, vp, vp, vp, i32, vp, sz, vp]
+        L.sc_residual_all.argtypes = [D, vp, vp, vp, i32, vp, vp, i32, vp, sz, vp]
         L.sc_lm_normal_eqs.argtypes = [D, vp, vp, vp, vp, vp, i32, vp, sz, vp]
         L.sc_solve_cluster.argtypes = [D, vp, vp, vp, _c.POINTER(LMOpts), vp, vp, i32, vp, sz, vp]
         L.sc_calibrate_sage.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, vp, _c.POINTER(SageOpts),
@@ -87,7 +93,7 @@ def lib():
         for f in ("sc_profile_begin", "sc_profile_end", "sc_profile_read"):
             getattr(L, f).restype = i32
         for f in ("sc_workspace_size", "sc_device_status", "sc_chol_schedule",
-                  "sc_predict_coherencies", "sc_residual", "sc_lm_normal_eqs",
+                  "sc_predict_coherencies", "sc_residual", "sc_residual_all", "sc_lm_normal_eqs",
                   "sc_solve_cluster", "sc_calibrate_sage"):
             getattr(L, f).restype = i32
         _LIB = L
@@ -263,6 +269,26 @@ def residual(shape: Shape, X, C, jones, prec: int, ws, out=None, want_cost=True)
     dc = d.c()
     _check(lib().sc_residual(_c.byref(dc), _ptr(X), _ptr(C), _ptr(jones), _ptr(out), _ptr(cost),
                              prec, _ptr(ws), ws.numel(), _stream()))
+    return out, cost
+
+
+def residual_all(shape: Shape, V, C, jones, prec: int, ws, corr=-1, out=None, want_cost=True):
+    """R = V - sum_k J_kp C_kpq J_kq^H over all K clusters, then, if corr >= 0,
+    R <- J_cp^{-1} R J_cq^{-H}; cost = sum |R|^2 before the correction
+    (device scalar).  out may be V (in place)."""
+    import torch
+    K = C.shape[0]
+    d = Shape(shape.N, shape.T, shape.F, K, shape.S_max)
+    _need(V, _cdt(prec), (d.T, d.B, d.F, 2, 2), "V")
+    _need(C, _cdt(prec), (K, d.T, d.B, d.F), "C")
+    _need(jones, torch.complex128, (K, d.N, 2, 2), "jones")
+    if out is None:
+        out = torch.empty_like(V)
+    _need(out, _cdt(prec), (d.T, d.B, d.F, 2, 2), "out")
+    cost = torch.zeros((), dtype=torch.float64, device=V.device) if want_cost else None
+    dc = d.c()
+    _check(lib().sc_residual_all(_c.byref(dc), _ptr(V), _ptr(C), _ptr(jones), int(corr), _ptr(out),
+                                 _ptr(cost), prec, _ptr(ws), ws.numel(), _stream()))
     return out, cost
 
 

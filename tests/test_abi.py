@@ -50,6 +50,25 @@ def test_host_only_calls(lib):
         sagecal.workspace_size(sagecal.Shape(N=8, T=10, F=1), 7)
 
 
+def test_residual_all_rejects_bad_arguments_before_touching_the_device(lib):
+    # the pointers are never dereferenced: every check below fails first
+    L = sagecal.lib()
+    d = sagecal.Shape(N=8, T=2, F=3, K=4, S_max=1).c()
+    fake = ctypes.c_void_p(1 << 20)
+    for corr in (-2, 4, 100):
+        rc = L.sc_residual_all(ctypes.byref(d), fake, fake, fake, corr, fake, None,
+                               sagecal.SC_MIXED, fake, 1 << 30, None)
+        assert rc == -1
+        buf = ctypes.create_string_buffer(256)
+        L.sc_last_error(buf, 256)
+        assert b"corr = %d" % corr in buf.value
+    rc = L.sc_residual_all(ctypes.byref(d), None, fake, fake, 0, fake, None, sagecal.SC_MIXED,
+                           fake, 1 << 30, None)
+    assert rc == -1
+    rc = L.sc_residual_all(ctypes.byref(d), fake, fake, fake, 0, fake, None, 5, fake, 1 << 30, None)
+    assert rc == -1
+
+
 def _documented_order(nT):
     """The factorisation list spelled out loop by loop: POTRF(0) and the
     TRSMs of column 0, then for each panel j the next column's updates,
