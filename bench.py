@@ -51,6 +51,10 @@ WORKLOADS = {
     "serve500": ("c5", 3, 10, "Poisson-arriving calibration jobs: stations uniform in {64,128,256,384,512}, "
                               "clusters 1-40 x 25 sources, 5-20 timeslots, 1-8 channels 140-160 MHz, 3 SAGE "
                               "sweeps x 10 LM, continuous batching with HBM-footprint admission"),
+    "chunks128": ("c2", 1, 10, "one 128-station sub-band (8128 baselines, 8 channels 140-160 MHz, 10 clusters x "
+                               "25 sources) in 6 consecutive chunks of 20 timeslots, gains drifting between "
+                               "chunks; each chunk 1 SAGE sweep x 10 LM warm-started from the previous chunk, "
+                               "all chunks in one sc_calibrate_chunks call"),
     "batch64": ("c3", 3, 10, "64 sub-band jobs of 256 stations (32640 baselines), timeslots uniform in 5-40 "
                              "per job, 1 channel, 20 clusters x 50 sources, 3 SAGE sweeps x 10 LM, all jobs "
                              "in one sc_calibrate_batch call"),
@@ -477,6 +481,146 @@ def run_batch(args, rank, world, local_rank):
         print(json.dumps(line))
 
 
+N_CHUNKS = 6
+CHUNK_DRIFT = 0.05   # rad per chunk: per-station gain phase drift, x_s in [0, 1]
+
+
+def run_chunks(args, rank, world, local_rank):
+    """One step = one sc_calibrate_chunks call over N_CHUNKS consecutive time
+    chunks of one sub-band, from identity gains, each chunk warm-started from
+    the previous one.  Also reports, outside the timed region, each chunk's
+    final cost against a cold start of the same budget and the noise floor."""
+    import dataclasses
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    sc.lib()
+    cfg, n_em, n_lm, desc = WORKLOADS["chunks128"]
+    prec = sc.SC_FP64 if args.prec == "fp64" else sc.SC_MIXED
+    spec = synth.config(cfg, seed=job_seed(rank))
+    n = N_CHUNKS
+    full = dataclasses.replace(spec, T=n * spec.T)
+    uvw = torch.as_tensor(synth.station_uvw(full)).to(dev)
+    freqs = torch.as_tensor(synth.freqs(spec)).to(dev)
+    dsky = sc.DeviceSky.from_synth(synth.sky(spec), dev)
+    shp = sc.Shape(spec.N, spec.T, spec.F, spec.K, spec.S)
+    ws = sc.workspace(shp, prec, dev)
+    Jt = torch.as_tensor(synth.jones_true(spec)).to(dev)
+    ph = torch.linspace(0.0, 1.0, spec.N, dtype=torch.float64, device=dev)[None, :, None, None]
+    p, q = np.triu_indices(spec.N, 1)
+    cdt = torch.complex64 if prec == sc.SC_MIXED else torch.complex128
+    rdt = torch.float32 if prec == sc.SC_MIXED else torch.float64
+    V = torch.zeros((n, spec.T, spec.B, spec.F, 2, 2), dtype=cdt, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(4321 + spec.seed)
+    for i in range(n):
+        C = sc.predict_coherencies(shp, uvw[i * spec.T:(i + 1) * spec.T].contiguous(), freqs, dsky, prec, ws)
+        Ji = Jt * torch.exp(1j * CHUNK_DRIFT * i * ph)
+        for k in range(spec.K):
+            G = (Ji[k, p] @ Ji[k, q].conj().transpose(-1, -2)).to(cdt)
+            V[i] += C[k][..., None, None] * G[None, :, None]
+        del C
+        V[i] += torch.view_as_complex(torch.randn((*V[i].shape, 2), generator=g, device=dev, dtype=rdt)
+                                      * spec.sigma)
+    J0 = torch.as_tensor(synth.identity_jones(spec.K, spec.N)).to(dev)
+    J = J0.clone()
+    units = spec.B * spec.T * spec.F * spec.K * n_lm * n_em * n
+    out = {}
+
+    def step():
+        J.copy_(J0)
+        out["r"] = sc.calibrate_chunks(shp, uvw, freqs, dsky, V, J, prec, ws, n_em=n_em, n_lm=n_lm,
+                                       refine_sweeps=args.refine, want_history=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    n0 = sc.launch_count()
+    sc.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = sc.profile_end()
+    n_launch = sc.launch_count() - n0
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = units * args.steps * world / (ms / 1e3)
+    warm = out["r"][2][:, -1].cpu().numpy()          # last cluster: the total residual after the sweep
+
+    # end to end: host data and uvw in, every chunk's solution and costs out
+    e2e = None
+    if not args.no_e2e:
+        hV, hu = V.cpu().pin_memory(), uvw.cpu().pin_memory()
+        hH = torch.empty((n, spec.K, spec.N, 2, 2), dtype=torch.complex128).pin_memory()
+        hC = torch.empty((n, spec.K), dtype=torch.float64).pin_memory()
+        dV, du = torch.empty_like(V), torch.empty_like(uvw)
+        bi = hV.numel() * hV.element_size() + hu.numel() * hu.element_size()
+        bo = hH.numel() * hH.element_size() + hC.numel() * hC.element_size()
+
+        def e2e_step():
+            dV.copy_(hV, non_blocking=True)
+            du.copy_(hu, non_blocking=True)
+            J.copy_(J0)
+            _, hist, costs = sc.calibrate_chunks(shp, du, freqs, dsky, dV, J, prec, ws, n_em=n_em, n_lm=n_lm,
+                                                 refine_sweeps=args.refine)
+            hH.copy_(hist, non_blocking=True)
+            hC.copy_(costs, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = max(1, min(args.steps, 3))
+        f0.record()
+        for _ in range(ks):
+            e2e_step()
+        f1.record()
+        torch.cuda.synchronize()
+        ems = max_over_ranks(f0.elapsed_time(f1), world, dev)
+        e2e = {"value": units * ks * world / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo), "steps": ks}
+
+    # cold starts with the same budget, outside the timed region
+    cold = []
+    for i in range(n):
+        Jc = J0.clone()
+        _, c = sc.calibrate_sage(shp, uvw[i * spec.T:(i + 1) * spec.T].contiguous(), freqs, dsky, V[i], Jc, prec,
+                                 ws, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
+        cold.append(float(c[-1].item()))
+    chi2 = 8.0 * spec.B * spec.T * spec.F * spec.sigma ** 2   # noise energy of one chunk
+    pk, src = peaks()
+    dominant = max(prof, key=lambda k: prof[k][1])
+    n_dom, ms_dom = prof[dominant]
+    roof = roofline_for(dominant, spec, prec, n_em, n_lm, n_dom, ms_dom, pk, src)
+    if roof.get("achieved") is not None and roof.get("peak"):
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update(kernel=dominant, launches=n_dom, avg_launch_us=1e3 * ms_dom / max(n_dom, 1),
+                share_of_step=ms_dom / ms if ms > 0 else None, traffic=None, peak_kind=src)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == sc.SC_MIXED else "f64",
+        "data": "synthetic (seeded stations, sky, drifting Jones and noise)",
+        "config": {"workload": "chunks128", "description": desc, "chunks": n, "timeslots_per_chunk": spec.T,
+                   "stations": spec.N, "channels": spec.F, "clusters": spec.K, "n_em": n_em, "n_lm": n_lm,
+                   "drift_rad_per_chunk": CHUNK_DRIFT, "precision": args.prec,
+                   "l2": "inputs larger than L2 (visibilities %.2f GB)" % (V.numel() * V.element_size() / 1e9)},
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(n_launch), "clocks": clk,
+        "warm_start": {"final_cost_warm": [float(x) for x in warm], "final_cost_cold": cold,
+                       "noise_floor_chi2": chi2,
+                       "note": "cost of the last cluster after each chunk's sweep = total residual energy"},
+        "kernel_ms": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def serve_spec(i, seed=0):
     """Shape of serving job i (uniform draws from the serving workload)."""
     u = synth.uniform(seed, synth.TAG_JOBS + 2, 5, offset=5 * i)
@@ -666,6 +810,8 @@ def main():
         if args.workload == "batch64":
             args.jobs = args.jobs or 64
             run_batch(args, rank, world, local_rank)
+        elif args.workload == "chunks128":
+            run_chunks(args, rank, world, local_rank)
         elif args.workload == "serve500":
             args.jobs = args.jobs or 500
             run_serve(args, rank, world, local_rank)

@@ -299,6 +299,33 @@ SC_API int32_t sc_calibrate_sage(const sc_dims* d, const double* uvw,
                                  int32_t prec, void* ws, size_t ws_bytes,
                                  void* stream);
 
+/* Consecutive time chunks of one observation (one sub-band), calibrated in
+ * order with the solver state kept on the device: chunk i runs
+ * sc_calibrate_sage on its own data, starting from the solution of chunk
+ * i-1 (chunk 0 from `jones`).  Gains drift slowly in time, so each chunk
+ * starts near its answer.  Every chunk's solution is written out and is
+ * the whole state of the run: calling again with jones = the solution of
+ * chunk i and the data of chunks i+1.. continues the run exactly (bit for
+ * bit, the kernels being deterministic).
+ *   d         shape of ONE chunk (d->T timeslots per chunk)
+ *   n_chunks  number of chunks, >= 1
+ *   uvw       DEVICE float64 [n_chunks * T][N][3]
+ *   freqs     DEVICE float64 [F], the same for every chunk
+ *   V         DEVICE [n_chunks][T][B][F][2][2] complex
+ *   jones     DEVICE complex128 [K][N][2][2]: initial guess in, solution of
+ *             the last chunk out
+ *   jones_out DEVICE out complex128 [n_chunks][K][N][2][2], the solution of
+ *             every chunk (the checkpoints); may be NULL
+ *   costs     DEVICE out float64 [n_chunks][K], final LM cost of each
+ *             cluster in the last sweep of each chunk; may be NULL
+ * Errors as sc_calibrate_sage; SC_EINVAL also for n_chunks < 1 or
+ * n_chunks * T > 65535. */
+SC_API int32_t sc_calibrate_chunks(const sc_dims* d, int32_t n_chunks, const double* uvw,
+                                   const double* freqs, const sc_sky* sky, const void* V,
+                                   double* jones, double* jones_out,
+                                   const sc_sage_opts* opts, double* costs, int32_t prec,
+                                   void* ws, size_t ws_bytes, void* stream);
+
 /* One job of a batch: the arguments of sc_calibrate_sage for one sub-band x
  * time chunk, with its own workspace and stream (jobs may differ in every
  * dimension). */

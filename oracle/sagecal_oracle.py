@@ -357,6 +357,22 @@ def sage_calibrate(V, Cs, J0, n_em, n_lm, tau=1e-3, eps_grad=1e-12,
     return J, costs
 
 
+def calibrate_chunks(Vs, Css, J0, n_em, n_lm, tau=1e-3, eps_grad=1e-12):
+    """Consecutive time chunks of one observation, calibrated in order: chunk
+    i runs sage_calibrate on its own data Vs[i] and coherencies Css[i],
+    starting from the solution of chunk i-1 (chunk 0 from J0).  The solution
+    of each chunk is the solver state carried forward, so restarting at
+    chunk i from the solution of chunk i-1 continues the run exactly.
+    Returns (J [n][K][N][2][2] per chunk, final LM costs [n][K])."""
+    J = np.array(J0, dtype=np.complex128)
+    Js, costs = [], []
+    for V, Cs in zip(Vs, Css):
+        J, c = sage_calibrate(V, Cs, J, n_em, n_lm, tau, eps_grad)
+        Js.append(J.copy())
+        costs.append(c)
+    return np.stack(Js), np.stack(costs)
+
+
 # --- comparison up to the unitary ambiguity -----------------------------------
 
 def align_unitary(J, J_ref):

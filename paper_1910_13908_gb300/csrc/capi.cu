@@ -512,6 +512,42 @@ SC_API int32_t sc_calibrate_sage(const sc_dims* d, const double* uvw, const doub
   return r ? r : ok();
 }
 
+SC_API int32_t sc_calibrate_chunks(const sc_dims* d, int32_t n_chunks, const double* uvw,
+                                   const double* freqs, const sc_sky* sky, const void* V,
+                                   double* jones, double* jones_out, const sc_sage_opts* opts,
+                                   double* costs, int32_t prec, void* ws, size_t ws_bytes,
+                                   void* stream) {
+  Ctx c;
+  // argument checks first: they touch no device memory
+  int r = check_dims(d, prec, c.s);
+  if (r) return r;
+  if (n_chunks < 1 || (int64_t)n_chunks * d->T > 65535)
+    return fail(SC_EINVAL, "n_chunks = %d: need 1 <= n_chunks and n_chunks * T <= 65535", n_chunks);
+  if ((r = check_sky(c.s, sky))) return r;
+  if (!opts) return fail(SC_EINVAL, "options are NULL");
+  if (opts->n_em < 0) return fail(SC_EINVAL, "n_em must be >= 0");
+  if ((r = check_lm(&opts->lm))) return r;
+  if (!uvw || !freqs || !V || !jones) return fail(SC_EINVAL, "uvw, freqs, V and jones must not be NULL");
+  if ((r = open_ctx(c, d, prec, ws, ws_bytes, stream))) return r;
+  const Shape& s = c.s;
+  const size_t rs = prec == SC_MIXED ? 4 : 8;
+  const size_t v_chunk = (size_t)s.T * s.B * s.F * 8 * rs;   // bytes of one chunk's data
+  const size_t u_chunk = (size_t)s.T * s.N * 3;              // doubles of one chunk's uvw
+  const size_t j_all = (size_t)s.K * s.N * 8;                // doubles of one Jones set
+  for (int i = 0; i < n_chunks; ++i) {
+    const void* Vi = static_cast<const char*>(V) + v_chunk * i;
+    double* ci = costs ? costs + (size_t)s.K * i : nullptr;
+    r = prec == SC_MIXED
+            ? sage<float>(c, uvw + u_chunk * i, freqs, sky, static_cast<const float*>(Vi), jones, *opts, ci)
+            : sage<double>(c, uvw + u_chunk * i, freqs, sky, static_cast<const double*>(Vi), jones, *opts, ci);
+    if (r) return r;
+    if (jones_out)
+      SC_CUDA(cudaMemcpyAsync(jones_out + j_all * i, jones, j_all * sizeof(double), cudaMemcpyDeviceToDevice,
+                              c.st));
+  }
+  return ok();
+}
+
 SC_API int32_t sc_calibrate_batch(const sc_job* jobs, int32_t n_jobs, const sc_sage_opts* opts, int32_t prec) {
   if (n_jobs < 0 || (n_jobs > 0 && jobs == nullptr)) return fail(SC_EINVAL, "bad job array");
   if (!opts) return fail(SC_EINVAL, "options are NULL");

@@ -86,6 +86,9 @@ def lib():
         L.sc_solve_cluster.argtypes = [D, vp, vp, vp, _c.POINTER(LMOpts), vp, vp, i32, vp, sz, vp]
         L.sc_calibrate_sage.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, vp, _c.POINTER(SageOpts),
                                         vp, i32, vp, sz, vp]
+        L.sc_calibrate_chunks.argtypes = [D, i32, vp, vp, _c.POINTER(SkyC), vp, vp, vp,
+                                          _c.POINTER(SageOpts), vp, i32, vp, sz, vp]
+        L.sc_calibrate_chunks.restype = i32
         L.sc_calibrate_batch.argtypes = [_c.POINTER(JobC), i32, _c.POINTER(SageOpts), i32]
         L.sc_calibrate_batch.restype = i32
         L.sc_launch_count.restype = _c.c_uint64
@@ -349,6 +352,32 @@ def calibrate_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int
                                    _ptr(jones), _c.byref(o), _ptr(costs), prec, _ptr(ws), ws.numel(),
                                    _stream()))
     return jones, costs
+
+
+def calibrate_chunks(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, ws, n_em=1,
+                     n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, max_ctas=0,
+                     want_history=True):
+    """Consecutive time chunks, each warm-started from the previous chunk's
+    solution.  shape.T is the timeslots of ONE chunk; V is
+    [n_chunks][T][B][F][2][2], uvw [n_chunks * T][N][3].  `jones` [K][N][2][2]
+    is the initial guess and is left holding the last chunk's solution.
+    Returns (jones, history [n_chunks][K][N][2][2] or None, costs [n_chunks][K])."""
+    import torch
+    K = sky.K
+    n = V.shape[0]
+    d = Shape(shape.N, shape.T, shape.F, K, max(shape.S_max, sky.S_max))
+    _need(uvw, torch.float64, (n * d.T, d.N, 3), "uvw")
+    _need(freqs, torch.float64, (d.F,), "freqs")
+    _need(V, _cdt(prec), (n, d.T, d.B, d.F, 2, 2), "V")
+    _need(jones, torch.complex128, (K, d.N, 2, 2), "jones")
+    hist = torch.empty((n, K, d.N, 2, 2), dtype=torch.complex128, device=V.device) if want_history else None
+    costs = torch.zeros((n, K), dtype=torch.float64, device=V.device)
+    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas))
+    dc, skc = d.c(), sky.c()
+    _check(lib().sc_calibrate_chunks(_c.byref(dc), int(n), _ptr(uvw), _ptr(freqs), _c.byref(skc),
+                                     _ptr(V), _ptr(jones), _ptr(hist), _c.byref(o), _ptr(costs), prec,
+                                     _ptr(ws), ws.numel(), _stream()))
+    return jones, hist, costs
 
 
 @dataclasses.dataclass

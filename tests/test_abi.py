@@ -69,6 +69,25 @@ def test_residual_all_rejects_bad_arguments_before_touching_the_device(lib):
     assert rc == -1
 
 
+def test_calibrate_chunks_rejects_bad_arguments_before_touching_the_device(lib):
+    L = sagecal.lib()
+    d = sagecal.Shape(N=8, T=2, F=1, K=1, S_max=1).c()
+    fake = ctypes.c_void_p(1 << 20)
+    offs = (ctypes.c_int32 * 2)(0, 1)
+    sky = sagecal.SkyC(offs, fake, fake, fake, fake, 150e6)
+    opts = sagecal.SageOpts(1, sagecal.lm_opts())
+    for n_chunks in (0, -3, 40000):
+        rc = L.sc_calibrate_chunks(ctypes.byref(d), n_chunks, fake, fake, ctypes.byref(sky), fake, fake,
+                                   None, ctypes.byref(opts), None, sagecal.SC_MIXED, fake, 1 << 30, None)
+        assert rc == -1
+        buf = ctypes.create_string_buffer(256)
+        L.sc_last_error(buf, 256)
+        assert b"n_chunks" in buf.value
+    rc = L.sc_calibrate_chunks(ctypes.byref(d), 2, fake, fake, ctypes.byref(sky), None, fake, None,
+                               ctypes.byref(opts), None, sagecal.SC_MIXED, fake, 1 << 30, None)
+    assert rc == -1
+
+
 def _documented_order(nT):
     """The factorisation list spelled out loop by loop: POTRF(0) and the
     TRSMs of column 0, then for each panel j the next column's updates,

@@ -13,8 +13,10 @@ oracle.  What differs is the arithmetic alone:
   e = |R' - R|_F bounded by the element tolerance (Cauchy-Schwarz), plus the
   float32 rounding of each |R|^2.
 Sizes: N = 37 and 70 (666 and 2415 baselines, several 256-thread blocks and a
-ragged last one), T*F = 6 (a ragged last slab of 4 visibilities), a cluster
-without sources, and N = 2, T = F = K = 1.  The full-size case runs the
+ragged last one), T*F = 6 and 5 (a ragged last slab of 4 visibilities), a
+cluster without sources, N = 2, T = F = K = 1, and K = 8, 9 (the complex64
+path streams the coherencies through its shared-memory ring once K reaches
+its 8 stages).  The full-size case runs the
 512-station, 40-cluster launch configuration the benchmark times.
 """
 import numpy as np
@@ -78,7 +80,8 @@ def run(prec, spec, Cs, V, J, corr, out_in_place=False):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N,T,F,K,counts", [(37, 3, 2, 3, [5, 0, 2]), (70, 2, 3, 4, None),
-                                            (2, 1, 1, 1, None)])
+                                            (2, 1, 1, 1, None), (37, 3, 2, 9, None),
+                                            (70, 1, 5, 8, None)])
 def test_residual_all_matches_oracle(prec, N, T, F, K, counts):
     spec, Cs, V, J = job(N, T, F, K, counts)
     # both sides see the same rounded inputs
