@@ -326,6 +326,40 @@ SC_API int32_t sc_calibrate_chunks(const sc_dims* d, int32_t n_chunks, const dou
                                    const sc_sage_opts* opts, double* costs, int32_t prec,
                                    void* ws, size_t ws_bytes, void* stream);
 
+/* A whole sc_calibrate_sage call recorded once as a CUDA graph and then
+ * replayed.  A job's launch sequence is fixed by its shape and options (the
+ * LM and SAGE loops run on the device, with no host decision between
+ * kernels), so one capture holds every kernel of the job: a replay costs
+ * one graph launch on the host instead of thousands of kernel launches,
+ * which is what bounds small jobs (64 stations, one cluster).
+ *
+ * The graph keeps the pointers, shapes, sky offsets and options given at
+ * capture.  To calibrate new data, write it into the same buffers (V, the
+ * initial guess in jones, uvw, the sky arrays) before the next replay; a
+ * replay then computes exactly what sc_calibrate_sage computes on those
+ * contents (bit for bit: same kernels, same order).  Nothing runs during
+ * the capture itself.
+ *
+ * sc_graph_capture_sage: arguments and errors as sc_calibrate_sage, plus
+ *   stream  a created stream (not NULL, the legacy default stream, which
+ *           cannot be captured), idle on this thread during the call
+ *   graph   HOST out: the handle, NULL on error
+ * Per-kernel profiling (sc_profile_begin) must be off.  The handle owns
+ * host-side driver resources only; it allocates no device memory.
+ * sc_graph_launch: replays the graph on `stream` (any stream of the device
+ *   it was captured on; NULL = legacy default stream), asynchronously.
+ *   Replays that share one workspace must not overlap on the device.
+ * sc_graph_destroy: releases the handle (NULL is ignored). */
+typedef struct sc_graph sc_graph;
+SC_API int32_t sc_graph_capture_sage(const sc_dims* d, const double* uvw,
+                                     const double* freqs, const sc_sky* sky,
+                                     const void* V, double* jones,
+                                     const sc_sage_opts* opts, double* costs,
+                                     int32_t prec, void* ws, size_t ws_bytes,
+                                     void* stream, sc_graph** graph);
+SC_API int32_t sc_graph_launch(sc_graph* graph, void* stream);
+SC_API int32_t sc_graph_destroy(sc_graph* graph);
+
 /* One job of a batch: the arguments of sc_calibrate_sage for one sub-band x
  * time chunk, with its own workspace and stream (jobs may differ in every
  * dimension). */

@@ -10,6 +10,7 @@
 #include <vector>
 #include <cstdio>
 #include <cstring>
+#include <new>
 
 #include "sc_common.cuh"
 
@@ -545,6 +546,83 @@ SC_API int32_t sc_calibrate_chunks(const sc_dims* d, int32_t n_chunks, const dou
       SC_CUDA(cudaMemcpyAsync(jones_out + j_all * i, jones, j_all * sizeof(double), cudaMemcpyDeviceToDevice,
                               c.st));
   }
+  return ok();
+}
+
+}  // extern "C"
+
+// A captured sc_calibrate_sage call: the instantiated graph, the device it
+// belongs to and the number of library kernels one replay launches.
+struct sc_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int device;
+  unsigned long long kernels;
+};
+
+extern "C" {
+
+SC_API int32_t sc_graph_capture_sage(const sc_dims* d, const double* uvw, const double* freqs,
+                                     const sc_sky* sky, const void* V, double* jones,
+                                     const sc_sage_opts* opts, double* costs, int32_t prec, void* ws,
+                                     size_t ws_bytes, void* stream, sc_graph** graph) {
+  if (graph == nullptr) return fail(SC_EINVAL, "graph is NULL");
+  *graph = nullptr;
+  if (stream == nullptr) return fail(SC_EINVAL, "capture needs a created stream, not the legacy default stream");
+  if (prof_active()) return fail(SC_EINVAL, "per-kernel profiling is on; call sc_profile_end() before capturing");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  SC_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(SC_EINVAL, "stream is already capturing");
+  int dev = 0;
+  SC_CUDA(cudaGetDevice(&dev));
+  const unsigned long long n0 = launch_count();
+  // relaxed: the first call on a device sets kernel attributes and queries
+  // occupancy, which are not stream work
+  SC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  const int r = sc_calibrate_sage(d, uvw, freqs, sky, V, jones, opts, costs, prec, ws, ws_bytes, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(st, &g);
+  if (r != SC_OK) {  // keeps sc_calibrate_sage's message
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (ee != cudaSuccess || g == nullptr) {
+    if (g) cudaGraphDestroy(g);
+    return fail(SC_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  if (ie != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(SC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+  }
+  sc_graph* h = new (std::nothrow) sc_graph{g, ex, dev, launch_count() - n0};
+  if (h == nullptr) {
+    cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(g);
+    return fail(SC_ENOMEM, "out of host memory for the graph handle");
+  }
+  *graph = h;
+  return ok();
+}
+
+SC_API int32_t sc_graph_launch(sc_graph* graph, void* stream) {
+  if (graph == nullptr) return fail(SC_EINVAL, "graph is NULL");
+  int dev = 0;
+  SC_CUDA(cudaGetDevice(&dev));
+  if (dev != graph->device)
+    return fail(SC_EINVAL, "graph captured on device %d, current device is %d", graph->device, dev);
+  SC_CUDA(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+  count_launches(graph->kernels);
+  return ok();
+}
+
+SC_API int32_t sc_graph_destroy(sc_graph* graph) {
+  if (graph == nullptr) return ok();
+  cudaGraphExecDestroy(graph->exec);
+  cudaGraphDestroy(graph->graph);
+  delete graph;
   return ok();
 }
 

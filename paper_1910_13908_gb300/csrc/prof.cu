@@ -63,6 +63,13 @@ void prof_stop(int kind, cudaStream_t st) {
 
 unsigned long long launch_count() { return g_launches.load(); }
 
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool prof_active() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
+
 int prof_begin() {
   std::lock_guard<std::mutex> lk(g_mu);
   g_recs.clear();

@@ -211,6 +211,8 @@ enum ProfKind {
 void prof_start(int kind, cudaStream_t st);
 void prof_stop(int kind, cudaStream_t st);  // also counts the launch
 unsigned long long launch_count();
+void count_launches(unsigned long long n);  // kernels launched by a graph replay
+bool prof_active();
 int prof_begin();
 int prof_end();
 void prof_read(int kind, long* n, double* ms);

@@ -90,6 +90,12 @@ def lib():
                                           _c.POINTER(SageOpts), vp, i32, vp, sz, vp]
         L.sc_calibrate_chunks.restype = i32
         L.sc_calibrate_batch.argtypes = [_c.POINTER(JobC), i32, _c.POINTER(SageOpts), i32]
+        L.sc_graph_capture_sage.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, vp, _c.POINTER(SageOpts),
+                                            vp, i32, vp, sz, vp, _c.POINTER(vp)]
+        L.sc_graph_launch.argtypes = [vp, vp]
+        L.sc_graph_destroy.argtypes = [vp]
+        for f in ("sc_graph_capture_sage", "sc_graph_launch", "sc_graph_destroy"):
+            getattr(L, f).restype = i32
         L.sc_calibrate_batch.restype = i32
         L.sc_launch_count.restype = _c.c_uint64
         L.sc_profile_read.argtypes = [i32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_double)]
@@ -378,6 +384,61 @@ def calibrate_chunks(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: i
                                      _ptr(V), _ptr(jones), _ptr(hist), _c.byref(o), _ptr(costs), prec,
                                      _ptr(ws), ws.numel(), _stream()))
     return jones, hist, costs
+
+
+class Graph:
+    """A sc_calibrate_sage call captured once as a CUDA graph (see
+    capture_sage).  launch() replays it on the current stream; the tensors
+    given at capture are kept alive here, since the graph reads and writes
+    them at every replay."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def launch(self):
+        if self._h is None:
+            raise RuntimeError("graph has been closed")
+        _check(lib().sc_graph_launch(self._h, _stream()))
+
+    def close(self):
+        if self._h is not None:
+            lib().sc_graph_destroy(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def capture_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, ws, costs, n_em=1,
+                 n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, max_ctas=0):
+    """Records calibrate_sage on these tensors as a CUDA graph (nothing runs
+    yet).  Each Graph.launch() then calibrates whatever V, jones (initial
+    guess in, solution out), uvw and the sky arrays hold at that point;
+    costs [K] float64 receives the final cluster costs.  Captured on a side
+    stream, since the legacy default stream cannot be captured."""
+    import torch
+    K = sky.K
+    d = Shape(shape.N, shape.T, shape.F, K, max(shape.S_max, sky.S_max))
+    _need(uvw, torch.float64, (d.T, d.N, 3), "uvw")
+    _need(freqs, torch.float64, (d.F,), "freqs")
+    _need(V, _cdt(prec), (d.T, d.B, d.F, 2, 2), "V")
+    _need(jones, torch.complex128, (K, d.N, 2, 2), "jones")
+    _need(costs, torch.float64, (K,), "costs")
+    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas))
+    dc, skc = d.c(), sky.c()
+    h = _c.c_void_p()
+    side = torch.cuda.Stream(device=V.device)
+    side.wait_stream(torch.cuda.current_stream(V.device))
+    with torch.cuda.stream(side):
+        _check(lib().sc_graph_capture_sage(_c.byref(dc), _ptr(uvw), _ptr(freqs), _c.byref(skc), _ptr(V),
+                                           _ptr(jones), _c.byref(o), _ptr(costs), prec, _ptr(ws),
+                                           ws.numel(), _c.c_void_p(side.cuda_stream), _c.byref(h)))
+    return Graph(h, (uvw, freqs, sky, V, jones, costs, ws))
 
 
 @dataclasses.dataclass

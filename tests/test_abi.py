@@ -138,3 +138,23 @@ def test_cholesky_task_order_respects_every_dependency():
         solve = sagecal.chol_schedule(nT, 1)
         assert [t[1] for t in solve] == list(range(nT)) + list(range(nT - 1, -1, -1))
         assert [t[0] for t in solve] == [3] * nT + [4] * nT
+
+
+def test_graph_calls_reject_bad_arguments_before_touching_the_device(lib):
+    # every check below fails before any CUDA call
+    L = sagecal.lib()
+    d = sagecal.Shape(N=8, T=2, F=3, K=1, S_max=1).c()
+    fake = ctypes.c_void_p(1 << 20)
+    o = sagecal.SageOpts(1, sagecal.lm_opts())
+    h = ctypes.c_void_p(123)
+    args = (ctypes.byref(d), fake, fake, None, fake, fake, ctypes.byref(o), None, sagecal.SC_MIXED, fake,
+            1 << 30)
+    assert L.sc_graph_capture_sage(*args, fake, None) == -1  # no place for the handle
+    # the legacy default stream cannot be captured; the handle is cleared
+    assert L.sc_graph_capture_sage(*args, None, ctypes.byref(h)) == -1
+    assert h.value is None
+    buf = ctypes.create_string_buffer(256)
+    L.sc_last_error(buf, 256)
+    assert b"legacy default stream" in buf.value
+    assert L.sc_graph_launch(None, None) == -1
+    assert L.sc_graph_destroy(None) == 0
