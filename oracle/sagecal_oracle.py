@@ -47,6 +47,15 @@ What pins each function (tests/test_oracle.py):
   minimum; a multistart search on 3 stations finds no lower cost.
 * sage_calibrate: K = 1 is the single-cluster LM bit for bit; noiseless
   multi-cluster recovery; the total cost never increases over EM sweeps.
+* predict_coherencies_full (polarised, extended sources): an unpolarised
+  point-source sky reduces it to predict_coherencies x Id; the Gaussian
+  visibility equals a brute-force quadrature of the Fourier integral of the
+  Gaussian brightness laid out with the stated axes and position angle
+  (elongated and rotated); a zero-size Gaussian is a point; rotating the
+  feeds by chi mixes (Q, U) by 2 chi and leaves I and V alone; the brightness
+  matrix is Hermitian with det I^2 - |p|^2 and trace 2I; swapping p and q
+  gives the conjugate transpose; linear in sources; the spectral law scales
+  all four Stokes parameters.
 * residual_all: against visibilities built one at a time with explicit 2x2
   products, removing every cluster leaves exactly the planted unmodelled
   signal A, and one cluster left in leaves its model; A seen through the gains
@@ -122,6 +131,90 @@ def predict_sky(uvw, freqs, sky):
     return np.stack([
         predict_coherencies(uvw, freqs, sky.l[a:b], sky.m[a:b], sky.flux[a:b],
                             sky.alpha[a:b], sky.f0)
+        for a, b in zip(sky.offsets[:-1], sky.offsets[1:])])
+
+
+# --- polarised and extended sources ------------------------------------------
+
+FWHM_PER_SIGMA = 2.0 * math.sqrt(2.0 * math.log(2.0))
+
+
+def brightness_matrix(I, Q, U, V):
+    """Source brightness (coherency) matrix in the linear-feed basis,
+    [S][2][2] complex:  [[I + Q, U + iV], [U - iV, I - Q]].
+
+    Unnormalised, so that an unpolarised source of flux I gives I * Id, the
+    coherency the point-source path uses; tr/2 = I, det = I^2 - Q^2 - U^2 - V^2.
+    """
+    I, Q, U, V = (np.asarray(a, dtype=np.float64) for a in (I, Q, U, V))
+    out = np.empty(I.shape + (2, 2), dtype=np.complex128)
+    out[..., 0, 0] = I + Q
+    out[..., 0, 1] = U + 1j * V
+    out[..., 1, 0] = U - 1j * V
+    out[..., 1, 1] = I - Q
+    return out
+
+
+def gaussian_visibility(u_lam, v_lam, maj, mnr, pa):
+    """Visibility of a unit-flux elliptical Gaussian at (u, v) in wavelengths:
+    the Fourier transform of exp(-(x_a^2 / sigma_a^2 + x_b^2 / sigma_b^2) / 2)
+    normalised to 1 at the origin,
+
+        exp(-2 pi^2 (sigma_a^2 u_a^2 + sigma_b^2 u_b^2)),
+
+    where sigma = FWHM / (2 sqrt(2 ln 2)), the major axis points along
+    (l, m) = (sin pa, cos pa) (position angle from +m towards +l), the minor
+    along (cos pa, -sin pa), and (u_a, u_b) are (u, v) projected on the same
+    two unit vectors.  Broadcasts; maj = mnr = 0 gives 1 (a point source).
+    """
+    sa = np.asarray(maj, dtype=np.float64) / FWHM_PER_SIGMA
+    sb = np.asarray(mnr, dtype=np.float64) / FWHM_PER_SIGMA
+    sp, cp = np.sin(pa), np.cos(pa)
+    ua = u_lam * sp + v_lam * cp
+    ub = u_lam * cp - v_lam * sp
+    return np.exp(-2.0 * np.pi ** 2 * (sa ** 2 * ua ** 2 + sb ** 2 * ub ** 2))
+
+
+def predict_coherencies_full(uvw, freqs, l, m, I, Q, U, V, alpha, maj, mnr, pa, f0=150e6):
+    """Full 2x2 coherencies of one cluster of polarised, possibly extended
+    sources, [T][B][F][2][2] complex128:
+
+        C_pq(t,f) = sum_s (f/f0)^alpha_s  G_s(u f/c, v f/c)
+                    exp(-2 pi i (f/c)(u l_s + v m_s + w (n_s - 1)))  B_s
+
+    with B_s = brightness_matrix(I_s, Q_s, U_s, V_s), G_s the Gaussian
+    visibility (gaussian_visibility; 1 for a point source) and (u, v, w) the
+    baseline uvw_p - uvw_q.  The shape is taken on the tangent plane at the
+    source (its visibility depends on u, v only).
+    """
+    uvw = np.asarray(uvw, dtype=np.float64)
+    T, N, _ = uvw.shape
+    p, q = baselines(N)
+    l = np.asarray(l, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    n = np.sqrt(1.0 - l * l - m * m)
+    Bs = brightness_matrix(I, Q, U, V)                         # [S][2][2]
+    F = len(freqs)
+    out = np.zeros((T, len(p), F, 2, 2), dtype=np.complex128)
+    for t in range(T):
+        b = uvw[t, p, :] - uvw[t, q, :]                       # [B][3]
+        path = (np.outer(b[:, 0], l) + np.outer(b[:, 1], m)
+                + np.outer(b[:, 2], n - 1.0))                 # [B][S] metres
+        for fi, f in enumerate(freqs):
+            spec = (f / f0) ** np.asarray(alpha, dtype=np.float64)          # [S]
+            G = gaussian_visibility(b[:, 0:1] * (f / C_LIGHT), b[:, 1:2] * (f / C_LIGHT),
+                                    maj, mnr, pa)              # [B][S]
+            w = np.exp(-2j * np.pi * (f / C_LIGHT) * path) * G * spec       # [B][S]
+            out[t, :, fi] = np.einsum("bs,sij->bij", w, Bs)
+    return out
+
+
+def predict_sky_full(uvw, freqs, sky):
+    """Full coherencies of every cluster of a `synth.PolSky`: [K][T][B][F][2][2]."""
+    return np.stack([
+        predict_coherencies_full(uvw, freqs, sky.l[a:b], sky.m[a:b], sky.I[a:b], sky.Q[a:b],
+                                 sky.U[a:b], sky.V[a:b], sky.alpha[a:b], sky.maj[a:b],
+                                 sky.mnr[a:b], sky.pa[a:b], sky.f0)
         for a, b in zip(sky.offsets[:-1], sky.offsets[1:])])
 
 

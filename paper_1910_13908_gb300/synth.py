@@ -44,6 +44,7 @@ TAG_JONES = 3
 TAG_NOISE = 4
 TAG_CENTRES = 5
 TAG_JOBS = 6
+TAG_POL = 7
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -223,6 +224,62 @@ def sky(spec: JobSpec, sources_per_cluster=None) -> Sky:
     flux = 10.0 ** (-1.0 + 2.0 * u[:, 2])
     alpha = np.full(S, spec.alpha)
     return Sky(l, m, flux, alpha, offsets)
+
+
+@dataclasses.dataclass
+class PolSky:
+    """Polarised and extended sources sorted by cluster (offsets as in Sky).
+
+    Per source: direction (l, m); Stokes I, Q, U, V in Jy at f0, all scaled
+    by (f/f0)^alpha; an elliptical Gaussian shape with full widths at half
+    maximum maj >= mnr (radians) and the position angle pa (radians, of the
+    major axis, from +m towards +l); maj = mnr = 0 is a point source."""
+    l: np.ndarray
+    m: np.ndarray
+    I: np.ndarray
+    Q: np.ndarray
+    U: np.ndarray
+    V: np.ndarray
+    alpha: np.ndarray
+    maj: np.ndarray
+    mnr: np.ndarray
+    pa: np.ndarray
+    offsets: np.ndarray
+    f0: float = F0
+
+    @property
+    def K(self) -> int:
+        return len(self.offsets) - 1
+
+    def cluster(self, k: int) -> "PolSky":
+        a, b = int(self.offsets[k]), int(self.offsets[k + 1])
+        cut = {f.name: getattr(self, f.name)[a:b] for f in dataclasses.fields(self)
+               if f.name not in ("offsets", "f0")}
+        return PolSky(**cut, offsets=np.array([0, b - a], dtype=np.int32), f0=self.f0)
+
+
+def sky_pol(spec: JobSpec, sources_per_cluster=None, frac_extended=0.3, max_lin_pol=0.2,
+            max_circ_pol=0.02, fwhm_arcmin=(0.2, 2.0)) -> PolSky:
+    """The sky of sky(spec) (same directions, I = flux, alpha), with
+    polarisation and shapes added: linear polarisation fraction uniform in
+    [0, max_lin_pol] at a uniform angle chi (Q = p I cos 2chi, U = p I sin
+    2chi), circular fraction uniform in [-max_circ_pol, max_circ_pol]; each
+    source extended with probability frac_extended, its major FWHM uniform
+    in fwhm_arcmin, minor = major x U(0.3, 1), position angle U(0, pi)."""
+    base = sky(spec, sources_per_cluster)
+    S = len(base.l)
+    u = uniform(spec.seed, TAG_POL, 7 * S).reshape(S, 7)
+    I = base.flux
+    p_lin = max_lin_pol * u[:, 0]
+    chi = np.pi * u[:, 1]
+    Q, U = p_lin * I * np.cos(2 * chi), p_lin * I * np.sin(2 * chi)
+    V = max_circ_pol * (2 * u[:, 2] - 1) * I
+    ext = u[:, 3] < frac_extended
+    lo, hi = (math.radians(a / 60.0) for a in fwhm_arcmin)
+    maj = np.where(ext, lo + (hi - lo) * u[:, 4], 0.0)
+    mnr = maj * (0.3 + 0.7 * u[:, 5])
+    pa = np.where(ext, np.pi * u[:, 6], 0.0)
+    return PolSky(base.l, base.m, I, Q, U, V, base.alpha, maj, mnr, pa, base.offsets, base.f0)
 
 
 def jones_true(spec: JobSpec) -> np.ndarray:
