@@ -271,6 +271,52 @@ def measure_residual_output(job, spec, prec, J, reps, pk, src, workload):
             "cost": float(cost.item()), "device_status": status}
 
 
+FLOPS_PER_POL_TERM = 22      # per (source, vis): e_p conj(e_q) (6) + 4 complex-by-real FMAs (16)
+FLOPS_PER_GAUSS_TERM = 10    # more per extended (source, vis): quadratic form (7) + attenuation (2) + 1
+
+
+def measure_predict_full(job, spec, prec, reps, pk):
+    """Polarised, Gaussian-extended prediction of every cluster
+    (sc_predict_coherencies_full) on the workload's sky with Stokes Q, U, V
+    and 30% of the sources Gaussian (synth.sky_pol), timed on its own.
+    ALU-bound: one complex product, four complex FMAs and, for an extended
+    source, one exponential per (source, vis)."""
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    sky = synth.sky_pol(spec)
+    dsky = sc.DeviceSkyFull.from_synth(sky, job["V"].device)
+    out = sc.predict_coherencies_full(job["shape"], job["uvw"], job["freqs"], dsky, prec, job["ws"])
+    torch.cuda.synchronize()
+    sc.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        sc.predict_coherencies_full(job["shape"], job["uvw"], job["freqs"], dsky, prec, job["ws"], out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = sc.profile_end()
+    status = sc.device_status(job["ws"])
+    n, kms = prof["coherency"]
+    vis = spec.B * spec.T * spec.F
+    n_src = int(sky.offsets[-1])
+    n_ext = int(np.count_nonzero((sky.maj != 0) | (sky.mnr != 0)))
+    terms = vis * n_src                                   # (source, vis) pairs of one call
+    flops = terms * FLOPS_PER_POL_TERM + vis * n_ext * FLOPS_PER_GAUSS_TERM
+    kern_s = kms / 1e3 / max(reps, 1)                     # contraction time of one call (all clusters)
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    del out
+    return {"call": "sc_predict_coherencies_full", "clusters": sky.K, "sources": n_src, "extended": n_ext,
+            "call_ms": round(e0.elapsed_time(e1) / reps, 4), "contraction_launches": n,
+            "contraction_ms_per_call": round(kern_s * 1e3, 4), "source_terms_per_s": terms / kern_s,
+            "roofline": {"bound": "alu", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / kern_s / 1e12 / peak,
+                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz,
+                         "flops_per_term": FLOPS_PER_POL_TERM, "extra_flops_per_extended_term":
+                         FLOPS_PER_GAUSS_TERM, "traffic": None},
+            "device_status": status}
+
+
 # DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/),
 # keyed by (kernel kind, workload); None until captured for the current kernel.
 NCU_TRAFFIC = {}
@@ -376,6 +422,9 @@ def run_ours(args, rank, world, local_rank):
     resid = None
     if not args.no_residual:
         resid = measure_residual_output(job, spec, prec, J, 5, pk, src, args.workload)
+    pol = None
+    if not args.no_pol:
+        pol = measure_predict_full(job, spec, prec, 3, pk)
     dominant = max(prof, key=lambda k: prof[k][1])
     n_dom, ms_dom = prof[dominant]
     roof = roofline_for(dominant, spec, prec, n_em, n_lm, n_dom, ms_dom, pk, src)
@@ -415,6 +464,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "fp64_gpu": fp64,
         "residual_output": resid,
+        "predict_full": pol,
         "graph": graph,
         "kernel_ms": breakdown,
         "final_costs_head": final_costs[:4],
@@ -877,6 +927,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
+    ap.add_argument("--no-pol", action="store_true",
+                    help="skip the timed polarised, extended-source prediction (sc_predict_coherencies_full)")
     ap.add_argument("--no-residual", action="store_true",
                     help="skip the timed residual output (sc_residual_all) after the steps")
     ap.add_argument("--jobs", type=int, default=0, help="jobs of the batch64 (64) / serve500 (500) workloads")

@@ -114,6 +114,27 @@ typedef struct sc_sky {
   double f0;              /* reference frequency, Hz */
 } sc_sky;
 
+/* Clustered sky model of polarised, possibly extended sources (SAGECal's
+ * sky models hold full Stokes and Gaussian sources besides points; the
+ * paper, §2, groups the sources of a model into clusters).  Sources of
+ * cluster k are [offsets[k], offsets[k+1]).  Each DEVICE array holds
+ * S_total float64 values. */
+typedef struct sc_sky_full {
+  const int32_t* offsets; /* HOST [K+1], offsets[0] = 0, non-decreasing */
+  const double* l;        /* direction cosine towards east */
+  const double* m;        /* direction cosine towards north */
+  const double* I;        /* Stokes I at f0, Jy */
+  const double* Q;        /* Stokes Q at f0, Jy */
+  const double* U;        /* Stokes U at f0, Jy */
+  const double* V;        /* Stokes V at f0, Jy */
+  const double* alpha;    /* spectral index of all four: S(f) = S (f/f0)^alpha */
+  const double* maj;      /* Gaussian FWHM along the major axis, radians (0: point) */
+  const double* mnr;      /* Gaussian FWHM along the minor axis, radians (0: point) */
+  const double* pa;       /* position angle of the major axis, radians, from
+                             +m (north) towards +l (east) */
+  double f0;              /* reference frequency, Hz */
+} sc_sky_full;
+
 /* Levenberg-Marquardt options (Madsen, Nielsen & Tingleff 2004, Alg. 3.16:
  * damping mu I, mu0 = tau max diag(J^T J), gain-ratio update of mu). */
 typedef struct sc_lm_opts {
@@ -186,6 +207,32 @@ SC_API int32_t sc_predict_coherencies(const sc_dims* d, const double* uvw,
                                       const double* freqs, const sc_sky* sky,
                                       void* C, int32_t prec, void* ws,
                                       size_t ws_bytes, void* stream);
+
+/* Step (a) for polarised and Gaussian-extended sources: the full 2x2
+ * coherency of every cluster,
+ *   C_pq(t,f) = sum_s (f/f0)^alpha_s G_s exp(-2 pi i f/c (u l + v m + w (n - 1))) B_s,
+ *   B_s = [[I + Q, U + iV], [U - iV, I - Q]]   (unnormalised: an unpolarised
+ *         source of flux I gives I * Id, as in sc_predict_coherencies),
+ *   G_s = exp(-2 pi^2 (sigma_a^2 u_a^2 + sigma_b^2 u_b^2)),
+ * sigma = FWHM / (2 sqrt(2 ln 2)), (u_a, u_b) the baseline (u, v) f/c in
+ * wavelengths projected on the major axis (sin pa, cos pa) and the minor
+ * axis (cos pa, -sin pa); G_s = 1 when maj = mnr = 0.  The shape is taken on
+ * the tangent plane at the source.
+ *   uvw, freqs  as sc_predict_coherencies
+ *   sky         polarised sky (offsets on the HOST, K = d->K clusters,
+ *               at most d->S_max sources per cluster)
+ *   C           DEVICE out [K][T][B][F][2][2] complex (complex64 SC_MIXED,
+ *               complex128 SC_FP64), the layout of the visibilities
+ * SC_MIXED: station phasors as sc_predict_coherencies; the spectral law and
+ * the Gaussian's quadratic form are folded per (channel, source) in float64
+ * and rounded; float32 attenuation and accumulation.  SC_FP64: everything
+ * in float64.  A cluster without sources predicts zeros.
+ * Errors: SC_EINVAL (NULL pointers, bad offsets, F * S_max > 2^30),
+ * SC_ENOMEM (workspace below sc_workspace_size for d). */
+SC_API int32_t sc_predict_coherencies_full(const sc_dims* d, const double* uvw,
+                                           const double* freqs, const sc_sky_full* sky,
+                                           void* C, int32_t prec, void* ws,
+                                           size_t ws_bytes, void* stream);
 
 /* Step (b): residual of one cluster, R = X - J_p (c Id) J_q^H, and its cost
  * sum |R|_F^2.

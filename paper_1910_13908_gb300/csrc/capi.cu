@@ -103,6 +103,7 @@ Workspace plan_workspace(const Shape& s, bool job) {
   L.gains = take(K * N * 8 * rs);
   L.gain_inv = take(N * 8 * rs);
   L.parts = take((size_t)kMaxParts * 8);
+  L.srcp = take(F * Smax * 32);
   L.total = o;
   return L;
 }
@@ -167,6 +168,23 @@ static int check_sky(const Shape& s, const sc_sky* sky) {
   return SC_OK;
 }
 
+static int check_sky_full(const Shape& s, const sc_sky_full* sky) {
+  if (sky == nullptr || sky->offsets == nullptr) return fail(SC_EINVAL, "sky or sky->offsets is NULL");
+  if (sky->offsets[0] != 0) return fail(SC_EINVAL, "sky->offsets[0] must be 0");
+  for (int k = 0; k < s.K; ++k) {
+    int n = sky->offsets[k + 1] - sky->offsets[k];
+    if (n < 0) return fail(SC_EINVAL, "sky->offsets decreases at cluster %d", k);
+    if (n > s.S_max) return fail(SC_EINVAL, "cluster %d has %d sources > S_max = %d", k, n, s.S_max);
+  }
+  if (sky->offsets[s.K] > 0 && (!sky->l || !sky->m || !sky->I || !sky->Q || !sky->U || !sky->V ||
+                                !sky->alpha || !sky->maj || !sky->mnr || !sky->pa))
+    return fail(SC_EINVAL, "sky source arrays must not be NULL");
+  if (!(sky->f0 > 0)) return fail(SC_EINVAL, "sky->f0 must be > 0");
+  if ((int64_t)s.F * std::max(s.S_max, 1) > (int64_t(1) << 30))
+    return fail(SC_EINVAL, "F * S_max = %lld exceeds 2^30", (long long)s.F * s.S_max);
+  return SC_OK;
+}
+
 static int check_lm(const sc_lm_opts* o) {
   if (o == nullptr) return fail(SC_EINVAL, "LM options are NULL");
   if (o->n_lm < 0 || o->refine_sweeps < 0 || o->refine_sweeps > 16)
@@ -207,6 +225,34 @@ static int predict_all(const Ctx& c, const double* uvw, const double* freqs, con
       }
       if (w_out)
         SC_LAUNCH(PK_OTHER, launch_w_from_C<R>(s, Ck, w_out + (size_t)s.B * k, c.st));
+    }
+  }
+  return SC_OK;
+}
+
+// Full 2x2 coherencies of every cluster of a polarised sky into C_out [K][T][B][F][2][2].
+template <typename R>
+static int predict_full_all(const Ctx& c, const double* uvw, const double* freqs, const sc_sky_full* sky,
+                            R* C_out) {
+  const Shape& s = c.s;
+  const size_t per = (size_t)s.T * s.B * s.F * 8;
+  for (int k = 0; k < s.K; ++k) {
+    const int a = sky->offsets[k], S = sky->offsets[k + 1] - a;
+    const SkyFull kf{sky->l + a, sky->m + a, sky->I + a, sky->Q + a, sky->U + a, sky->V + a,
+                     sky->alpha + a, sky->maj + a, sky->mnr + a, sky->pa + a, sky->f0};
+    R* Ck = C_out + per * k;
+    if (s.prec == SC_MIXED) {
+      float2* E = c.at<float2>(c.L.E);
+      float* Sf = c.at<float>(c.L.Sf);
+      float4* stp = c.at<float4>(c.L.srcp);
+      float4* gqp = stp + (size_t)s.F * std::max(s.S_max, 1);
+      SC_LAUNCH(PK_PHASORS, launch_station_phasors(s, uvw, freqs, kf.l, kf.m, kf.I, kf.alpha, kf.f0, S, E, Sf,
+                                                   c.st));
+      SC_LAUNCH(PK_OTHER, launch_source_params(s, S, freqs, kf, stp, gqp, c.st));
+      SC_LAUNCH(PK_COHERENCY,
+                launch_coherency_full_f32(s, S, uvw, E, stp, gqp, reinterpret_cast<float*>(Ck), c.st));
+    } else {
+      SC_LAUNCH(PK_COHERENCY, launch_predict_full_f64(s, S, uvw, freqs, kf, reinterpret_cast<double*>(Ck), c.st));
     }
   }
   return SC_OK;
@@ -434,6 +480,21 @@ SC_API int32_t sc_predict_coherencies(const sc_dims* d, const double* uvw, const
   if (!uvw || !freqs || !C) return fail(SC_EINVAL, "uvw, freqs and C must not be NULL");
   r = prec == SC_MIXED ? predict_all<float>(c, uvw, freqs, sky, static_cast<float*>(C), nullptr)
                        : predict_all<double>(c, uvw, freqs, sky, static_cast<double*>(C), nullptr);
+  return r ? r : ok();
+}
+
+SC_API int32_t sc_predict_coherencies_full(const sc_dims* d, const double* uvw, const double* freqs,
+                                           const sc_sky_full* sky, void* C, int32_t prec, void* ws,
+                                           size_t ws_bytes, void* stream) {
+  Ctx c;
+  // argument checks first: they touch no device memory
+  int r = check_dims(d, prec, c.s);
+  if (r) return r;
+  if ((r = check_sky_full(c.s, sky))) return r;
+  if (!uvw || !freqs || !C) return fail(SC_EINVAL, "uvw, freqs and C must not be NULL");
+  if ((r = open_ctx(c, d, prec, ws, ws_bytes, stream))) return r;
+  r = prec == SC_MIXED ? predict_full_all<float>(c, uvw, freqs, sky, static_cast<float*>(C))
+                       : predict_full_all<double>(c, uvw, freqs, sky, static_cast<double*>(C));
   return r ? r : ok();
 }
 

@@ -181,6 +181,8 @@ struct Workspace {
   size_t gains;      // [K][N][8] real, every cluster's Jones rounded to the data type
   size_t gain_inv;   // [N][8] real, inverse Jones of the correction direction
   size_t parts;      // [kMaxParts] double, per-block cost sums
+  // polarised prediction (sc_predict_coherencies_full)
+  size_t srcp;       // [2][F][S_max] float4: spectral Stokes, Gaussian quadratic form
   int nT, Ppad, nchunk, tchunk, splits;
 };
 
@@ -218,6 +220,20 @@ int prof_end();
 void prof_read(int kind, long* n, double* ms);
 
 // ---- launchers (internal; all asynchronous on `st`) -------------------------------------
+
+// one cluster of a polarised sky (device pointers at its first source)
+struct SkyFull {
+  const double *l, *m, *I, *Q, *U, *V, *alpha, *maj, *mnr, *pa;
+  double f0;
+};
+
+// predict_full.cu
+cudaError_t launch_source_params(const Shape& s, int S, const double* freqs, const SkyFull& k, float4* st,
+                                 float4* gq, cudaStream_t stream);
+cudaError_t launch_coherency_full_f32(const Shape& s, int S, const double* uvw, const float2* E,
+                                      const float4* st, const float4* gq, float* C, cudaStream_t stream);
+cudaError_t launch_predict_full_f64(const Shape& s, int S, const double* uvw, const double* freqs,
+                                    const SkyFull& k, double* C, cudaStream_t stream);
 
 // predict.cu
 cudaError_t launch_station_phasors(const Shape& s, const double* uvw, const double* freqs,

@@ -43,6 +43,12 @@ class SkyC(_c.Structure):
                 ("flux", _c.c_void_p), ("alpha", _c.c_void_p), ("f0", _c.c_double)]
 
 
+class SkyFullC(_c.Structure):
+    _fields_ = [("offsets", _c.POINTER(_c.c_int32))] + \
+        [(n, _c.c_void_p) for n in ("l", "m", "I", "Q", "U", "V", "alpha", "maj", "mnr", "pa")] + \
+        [("f0", _c.c_double)]
+
+
 class LMOpts(_c.Structure):
     _fields_ = [("n_lm", _c.c_int32), ("refine_sweeps", _c.c_int32),
                 ("tau", _c.c_double), ("eps_grad", _c.c_double),
@@ -80,6 +86,8 @@ def lib():
         L.sc_device_status.argtypes = [vp, sz, _c.POINTER(_c.c_uint32)]
         L.sc_chol_schedule.argtypes = [i32, i32, _c.POINTER(i32), i32]
         L.sc_predict_coherencies.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, i32, vp, sz, vp]
+        L.sc_predict_coherencies_full.argtypes = [D, vp, vp, _c.POINTER(SkyFullC), vp, i32, vp, sz, vp]
+        L.sc_predict_coherencies_full.restype = i32
         L.sc_residual.argtypes = [D, vp, vp, vp, vp, vp, i32, vp, sz, vp]
         L.sc_residual_all.argtypes = [D, vp, vp, vp, i32, vp, vp, i32, vp, sz, vp]
         L.sc_lm_normal_eqs.argtypes = [D, vp, vp, vp, vp, vp, i32, vp, sz, vp]
@@ -190,6 +198,39 @@ class DeviceSky:
                          [int(x) for x in sky.offsets], float(sky.f0))
 
 
+FULL_FIELDS = ("l", "m", "I", "Q", "U", "V", "alpha", "maj", "mnr", "pa")
+
+
+@dataclasses.dataclass
+class DeviceSkyFull:
+    """Polarised, possibly extended sky on the device: SoA float64 tensors
+    (FULL_FIELDS) + host cluster offsets."""
+    arrays: dict
+    offsets: list
+    f0: float = 150e6
+
+    def c(self):
+        offs = (_c.c_int32 * len(self.offsets))(*[int(x) for x in self.offsets])
+        s = SkyFullC(offs, *[_ptr(self.arrays[n]) for n in FULL_FIELDS], float(self.f0))
+        s._keep = offs
+        return s
+
+    @property
+    def K(self):
+        return len(self.offsets) - 1
+
+    @property
+    def S_max(self):
+        return max([b - a for a, b in zip(self.offsets[:-1], self.offsets[1:])] + [0])
+
+    @staticmethod
+    def from_synth(sky, device="cuda"):
+        import torch
+        t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
+        return DeviceSkyFull({n: t(getattr(sky, n)) for n in FULL_FIELDS},
+                             [int(x) for x in sky.offsets], float(sky.f0))
+
+
 def workspace_size(shape: Shape, prec: int) -> int:
     n = _c.c_size_t(0)
     d = shape.c()
@@ -262,6 +303,23 @@ def predict_coherencies(shape: Shape, uvw, freqs, sky: DeviceSky, prec: int, ws,
     dc, skc = d.c(), sky.c()
     _check(lib().sc_predict_coherencies(_c.byref(dc), _ptr(uvw), _ptr(freqs), _c.byref(skc),
                                         _ptr(out), prec, _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def predict_coherencies_full(shape: Shape, uvw, freqs, sky: DeviceSkyFull, prec: int, ws, out=None):
+    """Full 2x2 coherencies C [K][T][B][F][2][2] of a polarised, possibly
+    extended sky (sc_predict_coherencies_full)."""
+    import torch
+    K = sky.K
+    d = Shape(shape.N, shape.T, shape.F, K, max(shape.S_max, sky.S_max))
+    if out is None:
+        out = torch.empty((K, d.T, d.B, d.F, 2, 2), dtype=_cdt(prec), device=uvw.device)
+    _need(uvw, torch.float64, (d.T, d.N, 3), "uvw")
+    _need(freqs, torch.float64, (d.F,), "freqs")
+    _need(out, _cdt(prec), (K, d.T, d.B, d.F, 2, 2), "C")
+    dc, skc = d.c(), sky.c()
+    _check(lib().sc_predict_coherencies_full(_c.byref(dc), _ptr(uvw), _ptr(freqs), _c.byref(skc),
+                                             _ptr(out), prec, _ptr(ws), ws.numel(), _stream()))
     return out
 
 
