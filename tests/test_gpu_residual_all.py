@@ -14,9 +14,9 @@ oracle.  What differs is the arithmetic alone:
   float32 rounding of each |R|^2.
 Sizes: N = 37 and 70 (666 and 2415 baselines, several 256-thread blocks and a
 ragged last one), T*F = 6 and 5 (a ragged last slab of 4 visibilities), a
-cluster without sources, N = 2, T = F = K = 1, and K = 8, 9 (the complex64
-path streams the coherencies through its shared-memory ring once K reaches
-its 8 stages).  The full-size case runs the
+cluster without sources, N = 2, T = F = K = 1, and K = 4, 8, 9 (the
+complex64 path streams the coherencies through its 4-stage shared-memory
+ring once K reaches the stage count; K = 1 and 3 take the register kernel).  The full-size case runs the
 512-station, 40-cluster launch configuration the benchmark times.
 """
 import numpy as np
