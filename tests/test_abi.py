@@ -158,3 +158,29 @@ def test_graph_calls_reject_bad_arguments_before_touching_the_device(lib):
     assert b"legacy default stream" in buf.value
     assert L.sc_graph_launch(None, None) == -1
     assert L.sc_graph_destroy(None) == 0
+
+
+def test_predict_full_rejects_bad_arguments_before_touching_the_device(lib):
+    # the pointers are never dereferenced: every check below fails first
+    L = sagecal.lib()
+    fake = ctypes.c_void_p(1 << 20)
+
+    def call(d, offsets, fields=None, f0=150e6, C=fake):
+        offs = (ctypes.c_int32 * len(offsets))(*offsets)
+        ptrs = [fake] * 10 if fields is None else fields
+        sky = sagecal.SkyFullC(offs, *ptrs, f0)
+        return L.sc_predict_coherencies_full(ctypes.byref(d), fake, fake, ctypes.byref(sky), C,
+                                             sagecal.SC_MIXED, fake, 1 << 30, None)
+
+    d = sagecal.Shape(N=8, T=2, F=3, K=2, S_max=4).c()
+    assert call(d, [0, 2, 1]) == -1                       # offsets decrease
+    assert call(d, [1, 2, 3]) == -1                       # offsets[0] != 0
+    assert call(d, [0, 5, 6]) == -1                       # more sources than S_max
+    assert call(d, [0, 2, 4], fields=[fake] * 9 + [None]) == -1   # a NULL source array
+    assert call(d, [0, 2, 4], f0=0.0) == -1
+    assert call(d, [0, 2, 4], C=None) == -1
+    big = sagecal.Shape(N=8, T=1, F=40000, K=1, S_max=40000).c()
+    assert call(big, [0, 1]) == -1                        # F * S_max > 2^30
+    buf = ctypes.create_string_buffer(256)
+    L.sc_last_error(buf, 256)
+    assert b"F * S_max" in buf.value
