@@ -56,6 +56,14 @@ What pins each function (tests/test_oracle.py):
   matrix is Hermitian with det I^2 - |p|^2 and trace 2I; swapping p and q
   gives the conjugate transpose; linear in sources; the spectral law scales
   all four Stokes parameters.
+* penalised / lm_cluster(penalty=...): on a linear least-squares problem
+  the penalised LM reaches the closed form (A^T A + w I)^-1 (A^T b + w a).
+* consensus_fit: np.linalg.lstsq per parameter; exact on data that is a
+  polynomial of the basis.
+* consensus_calibrate: rho = 0 is independent SAGE per band; noiseless data
+  whose Jones vary along the basis is recovered with every penalty ~0;
+  consensus lowers the error of noisy sub-band solutions; a larger rho
+  shrinks the disagreement |J_f - basis[f] Z|.
 * residual_all: against visibilities built one at a time with explicit 2x2
   products, removing every cluster leaves exactly the planted unmodelled
   signal A, and one cluster left in leaves its model; A seen through the gains
@@ -412,14 +420,30 @@ def levenberg_marquardt(evaluate, theta0, n_iter, tau=1e-3, eps_grad=1e-12,
     return theta, cost, done
 
 
-def lm_cluster(X, C, J0, n_lm, tau=1e-3, eps_grad=1e-12, trace=None):
-    """Solve one cluster: minimise sum |X - C J_p J_q^H|^2 over the Jones.
-    Returns (J, final cost, iterations done)."""
+def penalised(evaluate, a, w):
+    """The least-squares problem of `evaluate` with the quadratic penalty
+    w |theta - a|^2 added, written as extra residual rows sqrt(w) (a - theta)
+    with unit Jacobian: cost + w |theta - a|^2, A + w I, g + w (a - theta)."""
+    a = np.asarray(a, dtype=np.float64)
+
+    def ev(theta):
+        cost, A, g = evaluate(theta)
+        d = theta - a
+        return cost + w * float(d @ d), A + w * np.eye(len(theta)), g - w * d
+    return ev
+
+
+def lm_cluster(X, C, J0, n_lm, tau=1e-3, eps_grad=1e-12, trace=None, penalty=None):
+    """Solve one cluster: minimise sum |X - C J_p J_q^H|^2 over the Jones,
+    plus w |J - A|_F^2 when penalty = (A [N][2][2], w) is given.
+    Returns (J, final cost (with the penalty), iterations done)."""
     def evaluate(theta):
         J = theta_to_jones(theta)
         R, cost = residual(X, C, J)
         A, g = normal_equations(R, C, J)
         return cost, A, g
+    if penalty is not None:
+        evaluate = penalised(evaluate, jones_to_theta(penalty[0]), penalty[1])
     theta, cost, done = levenberg_marquardt(evaluate, jones_to_theta(J0), n_lm,
                                             tau, eps_grad, trace)
     return theta_to_jones(theta), cost, done
@@ -428,11 +452,12 @@ def lm_cluster(X, C, J0, n_lm, tau=1e-3, eps_grad=1e-12, trace=None):
 # --- SAGE / EM ----------------------------------------------------------------
 
 def sage_calibrate(V, Cs, J0, n_em, n_lm, tau=1e-3, eps_grad=1e-12,
-                   sweep_costs=None):
+                   sweep_costs=None, penalties=None):
     """SAGE: for each EM iteration and each cluster k in ascending order, the
     E-step forms the data of cluster k, X_k = V - sum_{j != k} model_j, from
     the current solutions of the other clusters; the M-step solves cluster k
-    on X_k by LM, warm-started from its current Jones.
+    on X_k by LM, warm-started from its current Jones.  penalties[k] =
+    (A_k, w), if given, adds w |J_k - A_k|_F^2 to cluster k's LM cost.
     Returns (J [K][N][2][2], final LM cost of each cluster)."""
     K = len(Cs)
     J = np.array(J0, dtype=np.complex128)
@@ -443,7 +468,8 @@ def sage_calibrate(V, Cs, J0, n_em, n_lm, tau=1e-3, eps_grad=1e-12,
             for j in range(K):
                 if j != k:
                     X = X - model_vis(Cs[j], J[j])
-            J[k], costs[k], _ = lm_cluster(X, Cs[k], J[k], n_lm, tau, eps_grad)
+            pen = None if penalties is None else penalties[k]
+            J[k], costs[k], _ = lm_cluster(X, Cs[k], J[k], n_lm, tau, eps_grad, penalty=pen)
         if sweep_costs is not None:
             R = V - sum(model_vis(Cs[j], J[j]) for j in range(K))
             sweep_costs.append(float(np.sum(R.real ** 2 + R.imag ** 2)))
@@ -464,6 +490,62 @@ def calibrate_chunks(Vs, Css, J0, n_em, n_lm, tau=1e-3, eps_grad=1e-12):
         Js.append(J.copy())
         costs.append(c)
     return np.stack(Js), np.stack(costs)
+
+
+# --- consensus across sub-bands ------------------------------------------------
+
+def consensus_fit(Y, basis):
+    """The consensus step: the smooth frequency model that fits Y best, per
+    cluster and real parameter, in the least-squares sense over the bands.
+    Y [n_bands][K][N][2][2], basis [n_bands][n_poly]; returns Z
+    [K][n_poly][N][2][2] with sum_f |basis[f] Z - Y[f]|^2 minimal, from the
+    normal equations (B^T B) Z = B^T Y."""
+    B = np.asarray(basis, dtype=np.float64)
+    n_bands, n_poly = B.shape
+    rhs = np.einsum("fp,fknij->pknij", B, Y)
+    Z = np.linalg.solve(B.T @ B, rhs.reshape(n_poly, -1)).reshape(rhs.shape)
+    return np.ascontiguousarray(np.moveaxis(Z, 0, 1))
+
+
+def consensus_model(Z, basis):
+    """basis[f] Z for every band: [n_bands][K][N][2][2]."""
+    return np.einsum("fp,kpnij->fknij", np.asarray(basis, dtype=np.float64), Z)
+
+
+def consensus_calibrate(Vs, Css, J0s, basis, rho, n_admm, n_em, n_lm, tau=1e-3, eps_grad=1e-12,
+                        U0=None):
+    """Sub-band calibrations coupled by a smooth frequency model of the
+    Jones: consensus ADMM in scaled form (Boyd et al. 2011, §7.1) on
+    sum_f f_f(J_f) subject to J_f = basis[f] Z, with f_f the SAGE cost of
+    band f (sum |R|^2 over its data).  Each iteration:
+
+      J-step  every band runs SAGE (n_em sweeps, n_lm LM steps per cluster)
+              from its current Jones on f_f(J) + (rho/2) |J - (basis[f] Z - U_f)|^2;
+              in the first iteration the bands are calibrated alone (no
+              penalty: there is no Z yet);
+      Z-step  Z = consensus_fit(J + U, basis);
+      U-step  U_f += J_f - basis[f] Z.
+
+    Vs [n_bands] data, Css [n_bands][K][T][B][F] coherencies, J0s
+    [n_bands][K][N][2][2] initial Jones, U0 the initial scaled duals (zero
+    if None).  Returns (J, Z [K][n_poly][N][2][2], U, costs [n_bands][K]):
+    the final LM costs, penalty included."""
+    n_bands = len(Vs)
+    J = np.array(J0s, dtype=np.complex128)
+    U = np.zeros_like(J) if U0 is None else np.array(U0, dtype=np.complex128)
+    K, N = J.shape[1], J.shape[2]
+    n_poly = np.asarray(basis).shape[1]
+    Z = np.zeros((K, n_poly, N, 2, 2), dtype=np.complex128)
+    costs = np.zeros((n_bands, K))
+    for it in range(n_admm):
+        target = consensus_model(Z, basis) - U
+        for f in range(n_bands):
+            pens = None if it == 0 else [(target[f, k], 0.5 * rho) for k in range(K)]
+            J[f], costs[f] = sage_calibrate(Vs[f], Css[f], J[f], n_em, n_lm, tau, eps_grad,
+                                            penalties=pens)
+        Z = consensus_fit(J + U, basis)
+        U = U + J - consensus_model(Z, basis)
+    return J, Z, U, costs
 
 
 # --- comparison up to the unitary ambiguity -----------------------------------

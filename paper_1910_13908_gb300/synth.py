@@ -45,6 +45,7 @@ TAG_NOISE = 4
 TAG_CENTRES = 5
 TAG_JOBS = 6
 TAG_POL = 7
+TAG_BANDS = 8
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -288,6 +289,34 @@ def jones_true(spec: JobSpec) -> np.ndarray:
     s = math.sqrt(0.5 * spec.jones_var)
     pert = (z[0::2] + 1j * z[1::2]).reshape(spec.K, spec.N, 2, 2) * s
     return pert + np.eye(2)[None, None]
+
+
+def sub_bands(spec: JobSpec, n_bands: int, f_lo: float = 115e6, f_hi: float = 185e6):
+    """n_bands equal sub-bands tiling [f_lo, f_hi], each with spec.F equal
+    channels: ([n_bands][F] channel centres, [n_bands] band centres)."""
+    edges = np.linspace(f_lo, f_hi, n_bands + 1)
+    width = (edges[1:] - edges[:-1]) / spec.F
+    fr = edges[:-1, None] + width[:, None] * (np.arange(spec.F)[None, :] + 0.5)
+    return fr, 0.5 * (edges[:-1] + edges[1:])
+
+
+def frequency_basis(centres, n_poly: int, f_lo: float = 115e6, f_hi: float = 185e6) -> np.ndarray:
+    """[n_bands][n_poly] values of the powers x^0 .. x^(n_poly-1) of the
+    normalised frequency x = (f - f_mid) / (f_hi - f_mid) in [-1, 1] at each
+    band centre: the smooth frequency model the sub-band solutions share."""
+    x = (np.asarray(centres, dtype=np.float64) - 0.5 * (f_lo + f_hi)) / (0.5 * (f_hi - f_lo))
+    return x[:, None] ** np.arange(n_poly)[None, :]
+
+
+def jones_true_bands(spec: JobSpec, centres, drift_var: float = 0.02, f_lo: float = 115e6,
+                     f_hi: float = 185e6) -> np.ndarray:
+    """[n_bands][K][N][2][2] true Jones varying linearly across the band:
+    J(f) = jones_true(spec) + x(f) D, D = CN(0, drift_var) per entry, x the
+    normalised frequency of frequency_basis."""
+    z = normal(spec.seed, TAG_BANDS, 2 * 4 * spec.K * spec.N)
+    D = (z[0::2] + 1j * z[1::2]).reshape(spec.K, spec.N, 2, 2) * math.sqrt(0.5 * drift_var)
+    x = (np.asarray(centres, dtype=np.float64) - 0.5 * (f_lo + f_hi)) / (0.5 * (f_hi - f_lo))
+    return jones_true(spec)[None] + x[:, None, None, None, None] * D[None]
 
 
 def noise(spec: JobSpec, t0: int = 0, t1: int | None = None) -> np.ndarray:
