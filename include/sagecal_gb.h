@@ -87,6 +87,9 @@ extern "C" {
 #define SC_STATUS_SINGULAR 4u /* sc_residual_all: a Jones of the correction
                                  direction was singular; its baselines were
                                  zeroed */
+#define SC_STATUS_BASIS 8u    /* sc_calibrate_consensus: the normal matrix of
+                                 the frequency basis was singular; Z was set
+                                 to zero */
 
 typedef enum sc_precision {
   SC_FP64 = 0,  /* everything in float64 / complex128 */
@@ -406,6 +409,54 @@ SC_API int32_t sc_graph_capture_sage(const sc_dims* d, const double* uvw,
                                      void* stream, sc_graph** graph);
 SC_API int32_t sc_graph_launch(sc_graph* graph, void* stream);
 SC_API int32_t sc_graph_destroy(sc_graph* graph);
+
+/* Options of the consensus across sub-bands. */
+typedef struct sc_consensus_opts {
+  sc_sage_opts sage; /* the J-step: SAGE sweeps and LM options of every band */
+  int32_t n_admm;    /* consensus iterations (J-step, Z-step, dual step), >= 1 */
+  int32_t n_poly;    /* terms of the frequency basis, 1..8, <= n_bands */
+  double rho;        /* penalty parameter, >= 0 (0: the bands are independent) */
+} sc_consensus_opts;
+
+/* Sub-band calibrations coupled by a smooth frequency model of the Jones.
+ * SAGECal calibrates sub-bands in parallel on separate nodes and can tie
+ * their solutions together across frequency (paper §1, §2); the paper does
+ * not give that algorithm.  This is consensus ADMM in scaled form (Boyd,
+ * Parikh, Chu, Peleato & Eckstein 2011, §7.1) on
+ *     minimise sum_f f_f(J_f)  subject to  J_f = sum_p basis[f][p] Z_p,
+ * f_f the SAGE cost of band f (sum |R|^2 over its data).  Each iteration:
+ *   J-step  every band runs sc_calibrate_sage from its current Jones, with
+ *           (rho/2) |J_fk - a_fk|_F^2, a_f = basis[f] Z - U_f, added to the
+ *           LM cost of each cluster k (as residual rows: J^T J + (rho/2) I,
+ *           J^T r + (rho/2)(a - theta)); the first iteration has no
+ *           penalty (there is no Z yet), so each band starts alone;
+ *   Z-step  Z = (B^T B)^-1 B^T (J + U) per cluster and real parameter;
+ *   dual    U_f += J_f - basis[f] Z.
+ *   d        shape of ONE band: N, T, F channels per band, K, S_max
+ *   n_bands  sub-bands, n_poly..256
+ *   uvw      DEVICE float64 [T][N][3], the same for every band
+ *   freqs    DEVICE float64 [n_bands][F] channel frequencies of each band
+ *   sky      clustered sky model, the same for every band
+ *   V        DEVICE [n_bands][T][B][F][2][2] complex data of each band
+ *   basis    DEVICE float64 [n_bands][n_poly], e.g. powers of the
+ *            normalised band-centre frequency
+ *   jones    DEVICE complex128 [n_bands][K][N][2][2], initial guess in,
+ *            solution out
+ *   dual     DEVICE complex128 [n_bands][K][N][2][2] scaled duals U, in and
+ *            out (zero to start; passing the output of a previous call
+ *            back continues it)
+ *   Z        DEVICE out complex128 [K][n_poly][N][2][2], the frequency model
+ *   costs    DEVICE out float64 [n_bands][K], final LM cost of each cluster
+ *            in the last iteration, penalty included; may be NULL
+ * The bands run one after another on `stream`, sharing the workspace
+ * (sc_workspace_size of d).  Errors as sc_calibrate_sage; SC_EINVAL also for
+ * n_bands, n_poly, n_admm or rho out of range.  A singular B^T B raises
+ * SC_STATUS_BASIS and zeroes Z. */
+SC_API int32_t sc_calibrate_consensus(const sc_dims* d, int32_t n_bands, const double* uvw,
+                                      const double* freqs, const sc_sky* sky, const void* V,
+                                      const double* basis, double* jones, double* dual, double* Z,
+                                      double* costs, const sc_consensus_opts* opts, int32_t prec,
+                                      void* ws, size_t ws_bytes, void* stream);
 
 /* One job of a batch: the arguments of sc_calibrate_sage for one sub-band x
  * time chunk, with its own workspace and stream (jobs may differ in every

@@ -104,6 +104,7 @@ Workspace plan_workspace(const Shape& s, bool job) {
   L.gain_inv = take(N * 8 * rs);
   L.parts = take((size_t)kMaxParts * 8);
   L.srcp = take(F * Smax * 32);
+  L.pen = take(K * 8 * N * 8);
   L.total = o;
   return L;
 }
@@ -260,10 +261,12 @@ static int predict_full_all(const Ctx& c, const double* uvw, const double* freqs
 
 // Levenberg-Marquardt on one cluster.  Data: X = Xin (running = false) or
 // X = Xin + c J_old J_old^H with J_old the Jones at entry (running = true,
-// Xin being the residual of all clusters).  J_io [8N] in/out.
+// Xin being the residual of all clusters).  J_io [8N] in/out.  pen [8N],
+// if not NULL, adds pen_w |theta - pen|^2 to the cost.
 template <typename R>
 static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const R* w, double* J_io,
-                    const sc_lm_opts& o, double* cost_out, int32_t* iters_out) {
+                    const sc_lm_opts& o, double* cost_out, int32_t* iters_out, const double* pen = nullptr,
+                    double pen_w = 0.0) {
   const Shape& s = c.s;
   const Workspace& L = c.L;
   size_t n8 = (size_t)8 * s.N * sizeof(double);
@@ -294,7 +297,8 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   SC_CUDA(cudaMemsetAsync(rvec, 0, (size_t)L.Ppad * sizeof(double), c.st));
   SC_CUDA(cudaMemsetAsync(bw, 0, (size_t)L.Ppad * 2 * sizeof(R), c.st));  // no stale tag can match
   SC_LAUNCH(PK_PASS, launch_pass<R>(s, flags, Xin, C, J_old, J_cur, nullptr, stc, str, L.nchunk, L.tchunk, nullptr, c.st));
-  SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_cur, g_cur, H_cur, cp_cur, nullptr, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_cur, g_cur, H_cur, cp_cur, nullptr, pen,
+                                                pen_w, c.st));
   SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, H_cur, g_cur, cp_cur, J_cur, J_cur, c.st));
   for (int it = 0; it < o.n_lm; ++it) {
     SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, J_cur, H_cur, lm, A, true, false, c.st));
@@ -308,16 +312,19 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
     }
     SC_LAUNCH(PK_LM, launch_lm_trial(lm, s.N, L.Ppad, J_cur, x, H_cur, g_cur, J_trial, c.st));
     SC_LAUNCH(PK_PASS, launch_pass<R>(s, flags, Xin, C, J_old, J_trial, nullptr, stc, str, L.nchunk, L.tchunk, lm, c.st));
-    SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_trial, g_trial, H_trial, cp_trial, lm, c.st));
+    SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_trial, g_trial, H_trial, cp_trial, lm,
+                                                  pen, pen_w, c.st));
     SC_LAUNCH(PK_LM, launch_lm_decide(lm, s.N, cp_trial, J_cur, J_trial, g_cur, g_trial, H_cur, H_trial, c.st));
   }
   SC_LAUNCH(PK_LM, launch_lm_finish(lm, J_cur, s.N, J_io, cost_out, iters_out, c.st));
   return SC_OK;
 }
 
+// pen [K][8N], if not NULL, adds pen_w |J_k - pen_k|^2 to cluster k's LM cost.
 template <typename R>
 static int sage(const Ctx& c, const double* uvw, const double* freqs, const sc_sky* sky, const R* V,
-                double* jones, const sc_sage_opts& o, double* costs) {
+                double* jones, const sc_sage_opts& o, double* costs, const double* pen = nullptr,
+                double pen_w = 0.0) {
   const Shape& s = c.s;
   const Workspace& L = c.L;
   R* C = c.at<R>(L.C);
@@ -336,7 +343,8 @@ static int sage(const Ctx& c, const double* uvw, const double* freqs, const sc_s
     for (int k = 0; k < s.K; ++k) {
       double* Jk = jones + (size_t)8 * s.N * k;
       const R* Ck = C + perC * k;
-      r = lm_solve<R>(c, Rres, true, Ck, w + (size_t)s.B * k, Jk, o.lm, costs ? costs + k : nullptr, nullptr);
+      r = lm_solve<R>(c, Rres, true, Ck, w + (size_t)s.B * k, Jk, o.lm, costs ? costs + k : nullptr, nullptr,
+                      pen ? pen + (size_t)8 * s.N * k : nullptr, pen_w);
       if (r) return r;
       // R += c (J_old J_old^H - J_new J_new^H)
       SC_LAUNCH(PK_PASS, launch_pass<R>(s, P_OLD | P_SUB | P_WRITE_R, Rres, Ck, c.at<double>(L.J_old), Jk, Rres, nullptr,
@@ -390,7 +398,8 @@ static int normal_eqs_impl(const Ctx& c, const void* Rv, const void* C, const do
   SC_LAUNCH(PK_PASS, launch_pass<R>(s, P_STATS, static_cast<const R*>(Rv), static_cast<const R*>(C), nullptr, nullptr, nullptr,
                          c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, L.tchunk, nullptr, c.st));
   SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, w, jones, Jhr,
-                                   c.at<double>(L.H_cur), c.at<double>(L.cpart_cur), nullptr, c.st));
+                                   c.at<double>(L.H_cur), c.at<double>(L.cpart_cur), nullptr, nullptr, 0.0,
+                                   c.st));
   int P = 8 * s.N;
   SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, P, P, w, jones, c.at<double>(L.H_cur), nullptr, static_cast<R*>(JhJ), false, true,
                              c.st));
@@ -684,6 +693,57 @@ SC_API int32_t sc_graph_destroy(sc_graph* graph) {
   cudaGraphExecDestroy(graph->exec);
   cudaGraphDestroy(graph->graph);
   delete graph;
+  return ok();
+}
+
+SC_API int32_t sc_calibrate_consensus(const sc_dims* d, int32_t n_bands, const double* uvw,
+                                      const double* freqs, const sc_sky* sky, const void* V,
+                                      const double* basis, double* jones, double* dual, double* Z,
+                                      double* costs, const sc_consensus_opts* opts, int32_t prec,
+                                      void* ws, size_t ws_bytes, void* stream) {
+  Ctx c;
+  // argument checks first: they touch no device memory
+  int r = check_dims(d, prec, c.s);
+  if (r) return r;
+  if (!opts) return fail(SC_EINVAL, "options are NULL");
+  if (opts->n_poly < 1 || opts->n_poly > kMaxPoly)
+    return fail(SC_EINVAL, "n_poly = %d outside [1, %d]", opts->n_poly, kMaxPoly);
+  if (n_bands < opts->n_poly || n_bands > kMaxBands)
+    return fail(SC_EINVAL, "n_bands = %d outside [n_poly = %d, %d]", n_bands, opts->n_poly, kMaxBands);
+  if (opts->n_admm < 1) return fail(SC_EINVAL, "n_admm must be >= 1");
+  if (!(opts->rho >= 0) || !(opts->rho < 1e300)) return fail(SC_EINVAL, "rho must be finite and >= 0");
+  if (opts->sage.n_em < 0) return fail(SC_EINVAL, "n_em must be >= 0");
+  if ((r = check_lm(&opts->sage.lm))) return r;
+  if ((r = check_sky(c.s, sky))) return r;
+  if (!uvw || !freqs || !V || !basis || !jones || !dual || !Z)
+    return fail(SC_EINVAL, "uvw, freqs, V, basis, jones, dual and Z must not be NULL");
+  if ((r = open_ctx(c, d, prec, ws, ws_bytes, stream))) return r;
+  const Shape& s = c.s;
+  const int P = 8 * s.N, K = s.K, n_poly = opts->n_poly;
+  const size_t rs = prec == SC_MIXED ? 4 : 8;
+  const size_t v_band = (size_t)s.T * s.B * s.F * 8 * rs;  // bytes of one band's data
+  const size_t j_band = (size_t)K * P;                      // doubles of one band's Jones
+  double* target = c.at<double>(c.L.pen);
+  const double pen_w = 0.5 * opts->rho;
+  for (int it = 0; it < opts->n_admm; ++it) {
+    for (int f = 0; f < n_bands; ++f) {
+      const double* pen = nullptr;
+      if (it > 0) {
+        SC_LAUNCH(PK_OTHER, launch_consensus_target(f, n_poly, K, P, basis, Z, dual, target, c.st));
+        pen = target;
+      }
+      const void* Vf = static_cast<const char*>(V) + v_band * f;
+      double* cf = costs ? costs + (size_t)K * f : nullptr;
+      r = prec == SC_MIXED
+              ? sage<float>(c, uvw, freqs + (size_t)s.F * f, sky, static_cast<const float*>(Vf),
+                            jones + j_band * f, opts->sage, cf, pen, pen_w)
+              : sage<double>(c, uvw, freqs + (size_t)s.F * f, sky, static_cast<const double*>(Vf),
+                             jones + j_band * f, opts->sage, cf, pen, pen_w);
+      if (r) return r;
+    }
+    SC_LAUNCH(PK_OTHER, launch_consensus_fit(n_bands, n_poly, K, P, basis, jones, dual, Z, c.status(), c.st));
+    SC_LAUNCH(PK_OTHER, launch_consensus_dual(n_bands, n_poly, K, P, basis, jones, Z, dual, c.st));
+  }
   return ok();
 }
 

@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_station_reduce(int N, int64_
                                                         const double* __restrict__ J,
                                                         double* __restrict__ g, double* __restrict__ H,
                                                         double* __restrict__ cpart,
-                                                        const LMState* __restrict__ lm) {
+                                                        const LMState* __restrict__ lm,
+                                                        const double* __restrict__ pen, double pen_w) {
   if (lm != nullptr && (lm->done | lm->skip)) return;
   __shared__ double part[kReduceThreads / 32][13];
   int s = blockIdx.x;
@@ -200,6 +201,22 @@ __global__ void __launch_bounds__(kReduceThreads) k_station_reduce(int N, int64_
     double t = 0.0;
 #pragma unroll
     for (int w = 0; w < kReduceThreads / 32; ++w) t += part[w][i];
+    if (pen != nullptr) {
+      // quadratic penalty pen_w |theta_s - a_s|^2 as residual rows
+      // sqrt(pen_w) (a - theta): J^T r += pen_w (a - theta), the diagonal of
+      // H (hence of J^T J) += pen_w, cost += pen_w |theta - a|^2
+      const double* a = pen + 8 * s;
+      const double* th = J + 8 * s;
+      if (i < 8) {
+        t += pen_w * (a[i] - th[i]);
+      } else if (i < 10) {
+        t += pen_w;
+      } else if (i == 12) {
+        double e = 0.0;
+        for (int k = 0; k < 8; ++k) e += (th[k] - a[k]) * (th[k] - a[k]);
+        t += pen_w * e;
+      }
+    }
     if (i < 8) g[8 * s + i] = t;
     else if (i < 12) H[4 * s + i - 8] = t;
     else cpart[s] = t;
@@ -209,16 +226,20 @@ __global__ void __launch_bounds__(kReduceThreads) k_station_reduce(int N, int64_
 template <typename R>
 cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
                                   int nchunk, const R* w, const double* J, double* g, double* H,
-                                  double* cpart, const LMState* lm, cudaStream_t st) {
-  k_station_reduce<R><<<s.N, kReduceThreads, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm);
+                                  double* cpart, const LMState* lm, const double* pen, double pen_w,
+                                  cudaStream_t st) {
+  k_station_reduce<R><<<s.N, kReduceThreads, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm,
+                                                      pen, pen_w);
   return cudaGetLastError();
 }
 template cudaError_t launch_station_reduce<float>(const Shape&, const float*, const float*, int,
                                                   const float*, const double*, double*, double*,
-                                                  double*, const LMState*, cudaStream_t);
+                                                  double*, const LMState*, const double*, double,
+                                                  cudaStream_t);
 template cudaError_t launch_station_reduce<double>(const Shape&, const double*, const double*, int,
                                                    const double*, const double*, double*, double*,
-                                                   double*, const LMState*, cudaStream_t);
+                                                   double*, const LMState*, const double*, double,
+                                                   cudaStream_t);
 
 __global__ void k_sum_cost(const double* __restrict__ cpart, int N, double* __restrict__ out) {
   __shared__ double sh[32];

@@ -183,6 +183,8 @@ struct Workspace {
   size_t parts;      // [kMaxParts] double, per-block cost sums
   // polarised prediction (sc_predict_coherencies_full)
   size_t srcp;       // [2][F][S_max] float4: spectral Stokes, Gaussian quadratic form
+  // consensus across sub-bands (sc_calibrate_consensus)
+  size_t pen;        // [K][8N] double, penalty targets of one band's clusters
   int nT, Ppad, nchunk, tchunk, splits;
 };
 
@@ -227,6 +229,19 @@ struct SkyFull {
   double f0;
 };
 
+// consensus.cu: the Z-step, the penalty targets and the dual step of the
+// consensus across sub-bands; basis [n_bands][n_poly], Jones and duals
+// [n_bands][K][8N], Z [K][n_poly][8N] (all float64, device)
+constexpr int kMaxBands = 256;
+constexpr int kMaxPoly = 8;
+cudaError_t launch_consensus_fit(int n_bands, int n_poly, int K, int P, const double* basis,
+                                 const double* J, const double* U, double* Z, uint32_t* status,
+                                 cudaStream_t st);
+cudaError_t launch_consensus_target(int band, int n_poly, int K, int P, const double* basis,
+                                    const double* Z, const double* U, double* target, cudaStream_t st);
+cudaError_t launch_consensus_dual(int n_bands, int n_poly, int K, int P, const double* basis,
+                                  const double* J, const double* Z, double* U, cudaStream_t st);
+
 // predict_full.cu
 cudaError_t launch_source_params(const Shape& s, int S, const double* freqs, const SkyFull& k, float4* st,
                                  float4* gq, cudaStream_t stream);
@@ -259,7 +274,8 @@ cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, con
 template <typename R>
 cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
                                   int nchunk, const R* w, const double* J, double* g, double* H,
-                                  double* cpart, const LMState* lm, cudaStream_t st);
+                                  double* cpart, const LMState* lm, const double* pen, double pen_w,
+                                  cudaStream_t st);
 cudaError_t launch_sum_cost(const double* cpart, int N, double* out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sum_reals(const R* x, int64_t n, double* out, cudaStream_t st);

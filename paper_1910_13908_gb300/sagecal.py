@@ -28,6 +28,7 @@ SC_MIXED = 1
 SC_STATUS_NOTPD = 1
 SC_STATUS_TIMEOUT = 2
 SC_STATUS_SINGULAR = 4
+SC_STATUS_BASIS = 8
 
 _c = ctypes
 _LIB = None
@@ -57,6 +58,10 @@ class LMOpts(_c.Structure):
 
 class SageOpts(_c.Structure):
     _fields_ = [("n_em", _c.c_int32), ("lm", LMOpts)]
+
+
+class ConsensusOpts(_c.Structure):
+    _fields_ = [("sage", SageOpts), ("n_admm", _c.c_int32), ("n_poly", _c.c_int32), ("rho", _c.c_double)]
 
 
 class JobC(_c.Structure):
@@ -98,6 +103,9 @@ def lib():
                                           _c.POINTER(SageOpts), vp, i32, vp, sz, vp]
         L.sc_calibrate_chunks.restype = i32
         L.sc_calibrate_batch.argtypes = [_c.POINTER(JobC), i32, _c.POINTER(SageOpts), i32]
+        L.sc_calibrate_consensus.argtypes = [D, i32, vp, vp, _c.POINTER(SkyC), vp, vp, vp, vp, vp, vp,
+                                             _c.POINTER(ConsensusOpts), i32, vp, sz, vp]
+        L.sc_calibrate_consensus.restype = i32
         L.sc_graph_capture_sage.argtypes = [D, vp, vp, _c.POINTER(SkyC), vp, vp, _c.POINTER(SageOpts),
                                             vp, i32, vp, sz, vp, _c.POINTER(vp)]
         L.sc_graph_launch.argtypes = [vp, vp]
@@ -497,6 +505,38 @@ def capture_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, 
                                            _ptr(jones), _c.byref(o), _ptr(costs), prec, _ptr(ws),
                                            ws.numel(), _c.c_void_p(side.cuda_stream), _c.byref(h)))
     return Graph(h, (uvw, freqs, sky, V, jones, costs, ws))
+
+
+def calibrate_consensus(shape: Shape, uvw, freqs, sky: DeviceSky, V, basis, jones, prec: int, ws, rho,
+                        n_admm=3, n_em=1, n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, max_ctas=0,
+                        dual=None):
+    """Sub-band calibrations coupled by a smooth frequency model
+    (sc_calibrate_consensus).  shape is ONE band's (F channels per band);
+    freqs [n_bands][F], V [n_bands][T][B][F][2][2], basis [n_bands][n_poly]
+    float64, jones [n_bands][K][N][2][2] (updated in place), dual the scaled
+    duals (zeros if None; updated in place).
+    Returns (jones, dual, Z [K][n_poly][N][2][2], costs [n_bands][K])."""
+    import torch
+    K = sky.K
+    n_bands, n_poly = basis.shape
+    d = Shape(shape.N, shape.T, shape.F, K, max(shape.S_max, sky.S_max))
+    _need(uvw, torch.float64, (d.T, d.N, 3), "uvw")
+    _need(freqs, torch.float64, (n_bands, d.F), "freqs")
+    _need(V, _cdt(prec), (n_bands, d.T, d.B, d.F, 2, 2), "V")
+    _need(basis, torch.float64, (n_bands, n_poly), "basis")
+    _need(jones, torch.complex128, (n_bands, K, d.N, 2, 2), "jones")
+    if dual is None:
+        dual = torch.zeros_like(jones)
+    _need(dual, torch.complex128, (n_bands, K, d.N, 2, 2), "dual")
+    Z = torch.empty((K, n_poly, d.N, 2, 2), dtype=torch.complex128, device=V.device)
+    costs = torch.zeros((n_bands, K), dtype=torch.float64, device=V.device)
+    o = ConsensusOpts(SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas)), int(n_admm),
+                      int(n_poly), float(rho))
+    dc, skc = d.c(), sky.c()
+    _check(lib().sc_calibrate_consensus(_c.byref(dc), int(n_bands), _ptr(uvw), _ptr(freqs), _c.byref(skc),
+                                        _ptr(V), _ptr(basis), _ptr(jones), _ptr(dual), _ptr(Z), _ptr(costs),
+                                        _c.byref(o), prec, _ptr(ws), ws.numel(), _stream()))
+    return jones, dual, Z, costs
 
 
 @dataclasses.dataclass
