@@ -184,3 +184,32 @@ def test_predict_full_rejects_bad_arguments_before_touching_the_device(lib):
     buf = ctypes.create_string_buffer(256)
     L.sc_last_error(buf, 256)
     assert b"F * S_max" in buf.value
+
+
+def test_consensus_rejects_bad_arguments_before_touching_the_device(lib):
+    # the pointers are never dereferenced: every check below fails first
+    L = sagecal.lib()
+    fake = ctypes.c_void_p(1 << 20)
+    d = sagecal.Shape(N=8, T=2, F=3, K=2, S_max=4).c()
+    offs = (ctypes.c_int32 * 3)(0, 2, 4)
+    sky = sagecal.SkyC(offs, fake, fake, fake, fake, 150e6)
+
+    def call(n_bands=4, n_poly=2, n_admm=2, rho=1.0, basis=fake, dual=fake, opts=True):
+        o = sagecal.ConsensusOpts(sagecal.SageOpts(1, sagecal.lm_opts()), n_admm, n_poly, rho)
+        return L.sc_calibrate_consensus(ctypes.byref(d), n_bands, fake, fake, ctypes.byref(sky), fake, basis,
+                                        fake, dual, fake, None, ctypes.byref(o) if opts else None,
+                                        sagecal.SC_MIXED, fake, 1 << 30, None)
+
+    assert call(opts=False) == -1
+    assert call(n_poly=0) == -1
+    assert call(n_poly=9) == -1                           # at most 8 basis terms
+    assert call(n_bands=1, n_poly=2) == -1                # fewer bands than basis terms
+    assert call(n_bands=257) == -1                        # at most 256 bands
+    assert call(n_admm=0) == -1
+    assert call(rho=-1.0) == -1
+    assert call(rho=float("nan")) == -1
+    assert call(basis=None) == -1
+    assert call(dual=None) == -1
+    buf = ctypes.create_string_buffer(256)
+    L.sc_last_error(buf, 256)
+    assert b"must not be NULL" in buf.value
