@@ -848,7 +848,8 @@ def run_serve(args, rank, world, local_rank):
                    "arrival_rate_hz": rate, "single_stream_job_s": tau,
                    "rate_rule": "0.8 x measured single-stream capacity" if args.rate <= 0 else "given"},
         "serving": {"p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"], "mean_latency_s": st["mean_s"],
-                    "jobs_per_s": st["jobs_per_s"], "max_device_bytes_admitted": int(srv.max_used),
+                    "jobs_per_s": st["jobs_per_s"], "failed_jobs": st["failed"],
+                    "cancelled_jobs": st["cancelled"], "max_device_bytes_admitted": int(srv.max_used),
                     "budget_bytes": int(srv.mem_budget)},
         "gpu_launches": int(n_launch), "clocks": clk,
     }
