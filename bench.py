@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -119,9 +120,14 @@ def host_cores():
 # --- clocks during the timed region ------------------------------------------------------------
 
 class ClockSampler:
+    """nvidia-smi clock and throttle samples every 200 ms while the timed
+    region runs, written as CSV to $BENCH_CLOCKS_DIR (default: the system
+    temporary directory) and summarised into the JSON line."""
+
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        folder = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, "bench_clocks_%d.csv" % os.getpid())
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
