@@ -41,9 +41,12 @@
  * Memory and streams
  * ------------------
  *  All array pointers are DEVICE pointers owned by the caller unless marked
- *  HOST.  The library allocates no memory: every call that needs scratch
- *  takes a caller-owned device workspace (ws, ws_bytes) of at least
- *  sc_workspace_size() bytes, 256-byte aligned.  Every compute call is
+ *  HOST.  The library allocates no device memory: every call that needs
+ *  scratch takes a caller-owned device workspace (ws, ws_bytes) of at least
+ *  sc_workspace_size() bytes, 256-byte aligned (sc_residual_noalloc uses a
+ *  fixed array compiled into the library instead; a captured graph,
+ *  sc_graph_capture_sage, holds host-side driver resources until it is
+ *  destroyed).  Every compute call is
  *  asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream);
  *  outputs are valid once the stream has reached that point.  Calls that
  *  share one workspace must not overlap on the device.
