@@ -4,13 +4,20 @@ Tolerances (from the arithmetic of each path):
 * coherencies: FP64 path 1e-12 relative; mixed path 1e-5 relative, measured
   element-wise against the cluster's flux scale sum_s S_s(f) (the bound on
   |C|) and norm-wise against |C|;
-* residual, J^T J, J^T r: FP64 1e-11; mixed 1e-5 of the array's largest
+* residual, J^T J: FP64 1e-11; mixed 1e-5 of the array's largest
   magnitude (float32 data, float32 accumulation over T*F terms);
+* J^T r: FP64 1e-11 of its largest magnitude; mixed 1e-5 of the magnitudes
+  it sums per station (its float32 per-baseline sums round relative to
+  those; the sum over stations can cancel far below them);
 * final LM/SAGE cost within 1e-4 relative and Jones within 1e-4 after
   removing the unitary ambiguity (Procrustes), for both paths.
 Sizes span several 64-wide tiles with ragged tails (N = 37, 70: 8N = 296,
-560), odd T and F, a cluster without sources and N = 2.
+560), odd T and F, a cluster without sources and N = 2; the LM solve is also
+compared at the 512-station workload's factorisation order (8N = 4096) and
+at a ragged 8N = 2408.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -117,7 +124,21 @@ def test_normal_equations_match_oracle(prec, N):
     A, g = A.cpu().numpy().astype(np.float64), g.cpu().numpy()
     tol = 1e-11 if prec == sc.SC_FP64 else 1e-5
     assert np.max(np.abs(A - A_ref)) <= tol * np.max(np.abs(A_ref))
-    assert np.max(np.abs(g - g_ref)) <= (1e-11 if prec == sc.SC_FP64 else 2e-5) * np.max(np.abs(g_ref))
+    if prec == sc.SC_FP64:
+        assert np.max(np.abs(g - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+    else:
+        # Each entry of g_s sums, over the other stations o, float32 sums over
+        # (t, f) of conj(c) r multiplied by J_o.  Their rounding error is
+        # relative to the magnitudes summed, bounded per station by
+        # S_s = sum_o sum_tf |c| |r|_F |J_o|_F (about (T F + 2) eps_32 S_s);
+        # cancellation between stations can leave |g| itself far below S_s.
+        p, q = O.baselines(N)
+        mag = (np.abs(Cs[0]) * np.linalg.norm(R_ref, axis=(-2, -1))).sum(axis=(0, 2))    # [B]
+        jn = np.linalg.norm(J, axis=(1, 2))                                                # [N]
+        S = np.zeros(N)
+        np.add.at(S, p, mag * jn[q])
+        np.add.at(S, q, mag * jn[p])
+        assert np.all(np.abs(g - g_ref) <= 1e-5 * np.repeat(S, 8))
 
 
 # --- (c) LM solve of one cluster ----------------------------------------------------------------
@@ -145,6 +166,39 @@ def test_solve_cluster_matches_oracle(prec, N):
         assert abs(cost.item() - cost_ref) <= 1e-4 * cost_ref
         assert O.aligned_error(Jn, J_ref) <= 1e-4
         assert sc.device_status(ws) & 2 == 0
+
+
+@functools.lru_cache(maxsize=None)
+def _full_order_case(N, n_lm):
+    """One cluster of 100 sources on N stations, one timeslot and one channel
+    (the oracle's cost grows with the data, the factorisation's order 8N does
+    not), solved by the oracle from identity Jones with the gradient stop off."""
+    spec, uvw, f, sky, Jt, Cs, V = make_job(N=N, T=1, F=1, K=1, S=100, seed=5)
+    J0 = np.tile(np.eye(2, dtype=complex), (N, 1, 1))
+    J_ref, cost_ref, it_ref = O.lm_cluster(V, Cs[0], J0, n_lm, eps_grad=0.0)
+    return spec, Cs, V, J0, J_ref, cost_ref, it_ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,n_lm", [(512, 3), (301, 2)])
+def test_solve_cluster_full_order_matches_oracle(prec, N, n_lm):
+    """The LM solve at the factorisation order of the 512-station workload
+    (8N = 4096: 64 tile rows, the walker on the diagonal chain, the two-deep
+    bulk prefetch and the tagged-word solves across 64 block rows) and at a
+    ragged order (8N = 2408, padded to 2432 = 38 tile rows), against the
+    oracle: final cost within 1e-4 relative, Jones within 1e-4 after the
+    unitary alignment, the same number of LM steps.  With n_lm = 2 the
+    solution is still 1% above the minimum's cost, so both steps count."""
+    spec, Cs, V, J0, J_ref, cost_ref, it_ref = _full_order_case(N, n_lm)
+    shp = sc.Shape(N, 1, 1, 1, 100)
+    ws = sc.workspace(shp, prec)
+    Jg = tdev(J0, torch.complex128)
+    _, cost, iters = sc.solve_cluster(shp, tdev(V, cdt(prec)), tdev(Cs[0], cdt(prec)), Jg, prec, ws,
+                                      n_lm=n_lm, refine_sweeps=2, eps_grad=0.0)
+    assert iters.item() == it_ref == n_lm
+    assert abs(cost.item() - cost_ref) <= 1e-4 * cost_ref
+    assert O.aligned_error(Jg.cpu().numpy(), J_ref) <= 1e-4
+    assert sc.device_status(ws) == 0
 
 
 # --- the whole path ---------------------------------------------------------------------------
