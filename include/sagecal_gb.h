@@ -261,16 +261,26 @@ SC_API int32_t sc_residual(const sc_dims* d, const void* X, const void* C,
  * exists only for such callers.
  *
  * Same arguments, layouts and results as sc_residual, without the workspace
- * (the cost is summed in a different order, so it agrees to rounding).  Its
- * scratch is one 16 MiB array compiled into the library, which every GPU
- * that loads the library holds until the process exits.  Rules:
+ * (the cost is summed in a different order, so it agrees to rounding), and
+ * the same shape limits (N in [2, 8000], T*F <= 65535).  Its scratch is one
+ * 16 MiB array compiled into the library.  Rules:
+ *  - the array is device memory taken when the library's device code is
+ *    loaded on a GPU and held until the process exits.  Under CUDA's default
+ *    lazy module loading that is the first call of this function on the
+ *    device (CUDA_MODULE_LOADING=EAGER: context creation).  If your own
+ *    allocator will reserve the device, make one call first; otherwise that
+ *    first call fails with SC_ECUDA and an out-of-memory message;
  *  - with cost != NULL the problem may have at most 466026 baselines
  *    (N <= 965) in SC_MIXED and 233013 (N <= 683) in SC_FP64; larger ones
  *    are rejected with SC_EINVAL before anything is launched;
  *  - all calls on one device share the array, so calls that overlap on the
  *    GPU (other streams, other host threads) race; serialise them;
- *  - the first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture;
+ *  - every call made outside stream capture looks up the array's address in
+ *    the current CUDA context (cudaGetSymbolAddress), so a driver-API
+ *    context of the caller's or a device reset is followed.  A call made
+ *    during capture reuses the address found by the last call outside
+ *    capture on that device: make one call before capturing, in the context
+ *    the graph will run in;
  *  - nothing needs clearing between calls: each call writes all the scratch
  *    it then reads.
  * The error message of this call goes to errbuf (may be NULL), not to

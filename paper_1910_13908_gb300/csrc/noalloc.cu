@@ -11,8 +11,13 @@
 // nothing.
 //
 // Costs of the design, for the user:
-//  * every GPU that loads the library holds kScratchBytes of device memory
-//    until the process exits, whether or not the call is used;
+//  * every GPU on which the library's device code is loaded holds
+//    kScratchBytes of device memory until the process exits.  With CUDA's
+//    default lazy module loading that happens at the first call of this
+//    entry point on the device (its address lookup loads the module), with
+//    CUDA_MODULE_LOADING=EAGER when the context is created; either way it is
+//    the one allocation this design makes, so a caller whose allocator later
+//    reserves the device should make its first call before that;
 //  * all calls on one device share that array, so two calls that overlap on
 //    the GPU (other streams, other host threads) race and corrupt each
 //    other's cost; serialise them;
@@ -43,16 +48,34 @@ void* g_addr[kMaxDevices] = {};
 
 thread_local char g_nmsg[256] = "";
 
-// Device address of g_scratch on the current device; looked up once per
-// device (the first call on each device does this set-up).
-int scratch_address(void** out) {
+// Device address of g_scratch in the current context.  A module global has
+// its own address in every CUDA context (a new primary context after
+// cudaDeviceReset, or a driver-API context made current by a host
+// application), so the address is looked up again on every call made
+// outside stream capture.  During capture the address found by the last
+// call outside capture on this device is used (a lookup could load the
+// module, which is not stream work); with no such call yet the lookup is
+// tried once all the same.
+int scratch_address(cudaStream_t st, void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SC_ECUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    snprintf(g_nmsg, sizeof(g_nmsg), "sc_residual_noalloc: no usable current device (%s)",
+             e != cudaSuccess ? cudaGetErrorString(e) : "device ordinal out of range");
+    return SC_ECUDA;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (g_addr[dev] == nullptr) {
+  if (cs == cudaStreamCaptureStatusNone || g_addr[dev] == nullptr) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || p == nullptr) return SC_ECUDA;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      snprintf(g_nmsg, sizeof(g_nmsg),
+               "sc_residual_noalloc: cannot find its built-in scratch on device %d (cudaGetSymbolAddress: %s)",
+               dev, e != cudaSuccess ? cudaGetErrorString(e) : "null address");
+      return SC_ECUDA;
+    }
     g_addr[dev] = p;
   }
   *out = g_addr[dev];
@@ -78,10 +101,7 @@ int residual_noalloc(const Shape& s, const void* X, const void* C, const double*
   R* stat_rho = nullptr;
   if (cost != nullptr) {
     void* base = nullptr;
-    if (scratch_address(&base) != SC_OK) {
-      snprintf(g_nmsg, sizeof(g_nmsg), "sc_residual_noalloc: cudaGetSymbolAddress failed");
-      return SC_ECUDA;
-    }
+    if (scratch_address(st, &base) != SC_OK) return SC_ECUDA;
     stat_cost = static_cast<R*>(base);
     stat_rho = reinterpret_cast<R*>(static_cast<char*>(base) + ((s.B * sizeof(R) + 255) & ~(size_t)255));
   }
@@ -108,8 +128,11 @@ extern "C" SC_API int32_t sc_residual_noalloc(const sc_dims* d, const void* X, c
   if (d == nullptr || (prec != SC_FP64 && prec != SC_MIXED)) {
     snprintf(g_nmsg, sizeof(g_nmsg), "sc_residual_noalloc: bad dims or precision");
     rc = SC_EINVAL;
-  } else if (d->N < 2 || d->N > 8000 || d->T < 1 || d->F < 1) {
-    snprintf(g_nmsg, sizeof(g_nmsg), "sc_residual_noalloc: N must be in [2, 8000], T and F >= 1");
+  } else if (d->N < 2 || d->N > 8000 || d->T < 1 || d->F < 1 || (int64_t)d->T * d->F > 65535) {
+    // the same shape limits as sc_residual
+    snprintf(g_nmsg, sizeof(g_nmsg),
+             "sc_residual_noalloc: N must be in [2, 8000], T and F >= 1 and T*F <= 65535 "
+             "(N=%d T=%d F=%d)", d->N, d->T, d->F);
     rc = SC_EINVAL;
   } else if (!X || !C || !jones) {
     snprintf(g_nmsg, sizeof(g_nmsg), "sc_residual_noalloc: X, C and jones must not be NULL");
