@@ -79,6 +79,22 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def sm_count() -> int:
+    """Multiprocessors of the current CUDA device."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x SM clock (no measured FP32
+    figure exists, so it is derived from the unit counts)."""
+    return sm_count() * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak_source(sm_mhz: float) -> str:
+    return "FP32 FMA: %d SMs x 128 lanes x 2 flops x %.0f MHz" % (sm_count(), sm_mhz)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -214,9 +230,9 @@ def roofline_for(kind, spec, prec, n_em, n_lm, launches, ms, pk, peak_src):
     if kind == "cholesky":
         work = P ** 3 / 3.0                         # flops of L L^T = A
         if prec == sc.SC_MIXED:
-            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
+            peak = fp32_peak_tflops(sm_mhz)   # FP32 FMA lanes x 2 flops x clock
             return dict(bound="alu", achieved=work / avg_s / 1e12, peak=peak, unit="TFLOP/s",
-                        peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz)
+                        peak_source=fp32_peak_source(sm_mhz))
         peak = 1.25
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=peak, unit="TFLOP/s",
                     peak_source="FP64 nominal 1.25 TFLOP/s")
@@ -234,9 +250,9 @@ def roofline_for(kind, spec, prec, n_em, n_lm, launches, ms, pk, peak_src):
                     peak_source=peak_src)
     if kind == "coherency":
         work = 8.0 * vis * spec.S                        # one complex multiply-add per (source, vis)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        peak = fp32_peak_tflops(sm_mhz)
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=peak, unit="TFLOP/s",
-                    peak_source="FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz)
+                    peak_source=fp32_peak_source(sm_mhz))
     return dict(bound="latency", achieved=None, peak=None, unit=None)
 
 
@@ -310,14 +326,14 @@ def measure_predict_full(job, spec, prec, reps, pk):
     flops = terms * FLOPS_PER_POL_TERM + vis * n_ext * FLOPS_PER_GAUSS_TERM
     kern_s = kms / 1e3 / max(reps, 1)                     # contraction time of one call (all clusters)
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    peak = fp32_peak_tflops(sm_mhz)
     del out
     return {"call": "sc_predict_coherencies_full", "clusters": sky.K, "sources": n_src, "extended": n_ext,
             "call_ms": round(e0.elapsed_time(e1) / reps, 4), "contraction_launches": n,
             "contraction_ms_per_call": round(kern_s * 1e3, 4), "source_terms_per_s": terms / kern_s,
             "roofline": {"bound": "alu", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops / kern_s / 1e12 / peak,
-                         "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz,
+                         "peak_source": fp32_peak_source(sm_mhz),
                          "flops_per_term": FLOPS_PER_POL_TERM, "extra_flops_per_extended_term":
                          FLOPS_PER_GAUSS_TERM, "traffic": None},
             "device_status": status}

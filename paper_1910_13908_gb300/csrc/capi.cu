@@ -54,6 +54,30 @@ static int ok() {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Upper bound on the multiprocessor count the workspace layout allows for.
+constexpr int kMaxSMs = 512;
+
+// (timeslot, channel) splits of the point-source contraction: enough
+// (station tile pair, split) blocks for two per multiprocessor.
+static int coherency_splits(const Shape& s, int sms) {
+  const int nt = (s.N + 63) / 64, tiles = nt * (nt + 1) / 2;
+  return std::max(1, std::min(s.T * s.F, (2 * sms + tiles - 1) / tiles));
+}
+
+// Multiprocessors of the current device, looked up once per device.
+static int device_sms() {
+  constexpr int kDevs = 64;
+  static std::atomic<int> cache[kDevs];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) return 1;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+  v = std::min(v, kMaxSMs);
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 Workspace plan_workspace(const Shape& s, bool job) {
   Workspace L{};
   size_t rs = s.prec == SC_MIXED ? 4 : 8;
@@ -66,8 +90,10 @@ Workspace plan_workspace(const Shape& s, bool job) {
   int64_t tb = (int64_t)T * (int64_t)B;
   L.tchunk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)T, tb / target));
   L.nchunk = (int)((T + L.tchunk - 1) / L.tchunk);
-  int nt = (s.N + 63) / 64, tiles = nt * (nt + 1) / 2;
-  L.splits = std::max(1, std::min(s.T * s.F, (2 * 152 + tiles - 1) / tiles));
+  // room for the predict kernel's (timeslot, channel) splits on a GPU of up
+  // to kMaxSMs multiprocessors; the launch takes what the current device
+  // needs (coherency_splits), so the size does not depend on the device
+  L.splits = coherency_splits(s, kMaxSMs);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
@@ -133,6 +159,7 @@ struct Ctx {
   Workspace L;
   char* base;
   cudaStream_t st;
+  int splits;  // coherency splits for the current device (<= L.splits)
   template <class T>
   T* at(size_t off) const {
     return reinterpret_cast<T*>(base + off);
@@ -151,6 +178,7 @@ static int open_ctx(Ctx& c, const sc_dims* d, int32_t prec, void* ws, size_t ws_
     return fail(SC_ENOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, c.L.total);
   c.base = static_cast<char*>(ws);
   c.st = static_cast<cudaStream_t>(stream);
+  c.splits = std::min(c.L.splits, coherency_splits(c.s, device_sms()));
   SC_CUDA(cudaMemsetAsync(c.status(), 0, 256, c.st));
   return SC_OK;
 }
@@ -213,9 +241,9 @@ static int predict_all(const Ctx& c, const double* uvw, const double* freqs, con
       float* wpart = c.at<float>(c.L.wpart);
       SC_LAUNCH(PK_PHASORS, launch_station_phasors(s, uvw, freqs, sky->l + a, sky->m + a, sky->flux + a,
                                      sky->alpha + a, sky->f0, S, E, Sf, c.st));
-      SC_LAUNCH(PK_COHERENCY, launch_coherency_f32(s, S, E, Sf, reinterpret_cast<float2*>(Ck), wpart, c.L.splits, c.st));
+      SC_LAUNCH(PK_COHERENCY, launch_coherency_f32(s, S, E, Sf, reinterpret_cast<float2*>(Ck), wpart, c.splits, c.st));
       if (w_out)
-        SC_LAUNCH(PK_OTHER, launch_sum_parts(wpart, c.L.splits, s.B, reinterpret_cast<float*>(w_out) + (size_t)s.B * k,
+        SC_LAUNCH(PK_OTHER, launch_sum_parts(wpart, c.splits, s.B, reinterpret_cast<float*>(w_out) + (size_t)s.B * k,
                                  c.st));
     } else {
       if (S > 0) {
