@@ -236,8 +236,12 @@ def roofline_for(kind, spec, prec, n_em, n_lm, launches, ms, pk, peak_src):
         peak = 1.25
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=peak, unit="TFLOP/s",
                     peak_source="FP64 nominal 1.25 TFLOP/s")
+    if kind == "lm_stats":
+        work = vis * (4 * 2 * rs + 2 * rs)               # read the data (2x2 complex) + coherency, once per solve
+        return dict(bound="hbm", achieved=work / avg_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
+                    peak_source=peak_src)
     if kind == "vis_pass":
-        work = vis * (4 * 2 * rs + 2 * rs)               # read residual (2x2 complex) + coherency
+        work = vis * (2 * 4 * 2 * rs + 2 * rs)           # read and write the running residual, read the coherency
         return dict(bound="hbm", achieved=work / avg_s / 1e9, peak=pk["hbm_gbs"], unit="GB/s",
                     peak_source=peak_src)
     if kind == "jhj_assemble":
@@ -459,6 +463,15 @@ def run_ours(args, rank, world, local_rank):
     roof["traffic"] = NCU_TRAFFIC.get((dominant, args.workload))
     roof["peak_kind"] = src
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}
+    # the streaming kernels' own rooflines (HBM-bound)
+    streaming = {}
+    for k in ("lm_stats", "vis_pass"):
+        if prof.get(k, (0, 0))[0]:
+            r = roofline_for(k, spec, prec, n_em, n_lm, prof[k][0], prof[k][1], pk, src)
+            r["frac"] = r["achieved"] / r["peak"]
+            r["avg_launch_us"] = 1e3 * prof[k][1] / prof[k][0]
+            r["launches"] = prof[k][0]
+            streaming[k] = r
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -489,6 +502,7 @@ def run_ours(args, rank, world, local_rank):
         "predict_full": pol,
         "graph": graph,
         "kernel_ms": breakdown,
+        "streaming": streaming,
         "final_costs_head": final_costs[:4],
     }
     if flush is not None:

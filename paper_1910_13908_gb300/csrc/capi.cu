@@ -54,9 +54,6 @@ static int ok() {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Upper bound on the multiprocessor count the workspace layout allows for.
-constexpr int kMaxSMs = 512;
-
 // (timeslot, channel) splits of the point-source contraction: enough
 // (station tile pair, split) blocks for two per multiprocessor.
 static int coherency_splits(const Shape& s, int sms) {
@@ -110,6 +107,8 @@ Workspace plan_workspace(const Shape& s, bool job) {
   L.Sf = take(F * Smax * 8);
   L.stat_cost = take((size_t)L.nchunk * B * rs);
   L.stat_rho = take((size_t)L.nchunk * B * 8 * rs);
+  L.lstat = take(lm_stats_doubles(s.T, s.B) * 8);
+  L.part = take(lm_part_doubles(s.N) * 8);
   L.J_old = take(8 * N * 8);
   L.J_cur = take(8 * N * 8);
   L.J_trial = take(8 * N * 8);
@@ -121,7 +120,7 @@ Workspace plan_workspace(const Shape& s, bool job) {
   L.cpart_trial = take(N * 8);
   L.x = take((size_t)L.Ppad * 8);
   L.rvec = take((size_t)L.Ppad * 8);
-  L.corr = take((size_t)L.Ppad * 8);
+  L.ry = take((size_t)L.Ppad * 8);
   L.bvec = take((size_t)L.Ppad * 2 * rs);
   L.A = take((size_t)L.Ppad * L.Ppad * rs);
   L.Linv = take((size_t)L.nT * kNB * kNB * rs);
@@ -309,14 +308,13 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   double* cp_trial = c.at<double>(L.cpart_trial);
   double* x = c.at<double>(L.x);
   double* rvec = c.at<double>(L.rvec);
-  R* stc = c.at<R>(L.stat_cost);
-  R* str = c.at<R>(L.stat_rho);
+  double* stat = c.at<double>(L.lstat);
+  double* part = c.at<double>(L.part);
   R* A = c.at<R>(L.A);
   R* Linv = c.at<R>(L.Linv);
   uint64_t* bw = c.at<uint64_t>(L.bvec);
   int* sync = c.at<int>(L.sync);
   LMState* lm = c.lm();
-  const int flags = running ? (P_OLD | P_SUB | P_STATS) : (P_SUB | P_STATS);
   const bool mixed = s.prec == SC_MIXED;
 
   SC_CUDA(cudaMemcpyAsync(J_old, J_io, n8, cudaMemcpyDeviceToDevice, c.st));
@@ -324,9 +322,10 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   SC_CUDA(cudaMemsetAsync(x, 0, (size_t)L.Ppad * sizeof(double), c.st));
   SC_CUDA(cudaMemsetAsync(rvec, 0, (size_t)L.Ppad * sizeof(double), c.st));
   SC_CUDA(cudaMemsetAsync(bw, 0, (size_t)L.Ppad * 2 * sizeof(R), c.st));  // no stale tag can match
-  SC_LAUNCH(PK_PASS, launch_pass<R>(s, flags, Xin, C, J_old, J_cur, nullptr, stc, str, L.nchunk, L.tchunk, nullptr, c.st));
-  SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_cur, g_cur, H_cur, cp_cur, nullptr, pen,
-                                                pen_w, c.st));
+  int nst = 0;  // timeslot chunks of the statistics
+  SC_LAUNCH(PK_STATS, launch_lm_stats<R>(s, Xin, C, running ? J_old : nullptr, stat, &nst, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, nst, J_cur, part, nullptr, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, J_cur, g_cur, H_cur, cp_cur, nullptr, pen, pen_w, c.st));
   SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, H_cur, g_cur, cp_cur, J_cur, J_cur, c.st));
   for (int it = 0; it < o.n_lm; ++it) {
     SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, J_cur, H_cur, lm, A, true, false, c.st));
@@ -334,14 +333,14 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
     SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, g_cur, bw, x, 0, c.status(), lm, c.st));
     if (mixed) {
       for (int sw = 0; sw < o.refine_sweeps; ++sw) {
-        SC_LAUNCH(PK_REFINE, launch_refine_residual<R>(s, w, J_cur, H_cur, g_cur, x, lm, rvec, c.st));
+        SC_LAUNCH(PK_REFINE, launch_refine_residual<R>(s, w, J_cur, H_cur, g_cur, x, lm, c.at<double>(L.ry), rvec,
+                                                       c.st));
         SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, rvec, bw, x, 1, c.status(), lm, c.st));
       }
     }
     SC_LAUNCH(PK_LM, launch_lm_trial(lm, s.N, L.Ppad, J_cur, x, H_cur, g_cur, J_trial, c.st));
-    SC_LAUNCH(PK_PASS, launch_pass<R>(s, flags, Xin, C, J_old, J_trial, nullptr, stc, str, L.nchunk, L.tchunk, lm, c.st));
-    SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, stc, str, L.nchunk, w, J_trial, g_trial, H_trial, cp_trial, lm,
-                                                  pen, pen_w, c.st));
+    SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, nst, J_trial, part, lm, c.st));
+    SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, J_trial, g_trial, H_trial, cp_trial, lm, pen, pen_w, c.st));
     SC_LAUNCH(PK_LM, launch_lm_decide(lm, s.N, cp_trial, J_cur, J_trial, g_cur, g_trial, H_cur, H_trial, c.st));
   }
   SC_LAUNCH(PK_LM, launch_lm_finish(lm, J_cur, s.N, J_io, cost_out, iters_out, c.st));
@@ -423,11 +422,14 @@ static int normal_eqs_impl(const Ctx& c, const void* Rv, const void* C, const do
   const Shape& s = c.s;
   R* w = c.at<R>(L.w);
   SC_LAUNCH(PK_OTHER, launch_w_from_C<R>(s, static_cast<const R*>(C), w, c.st));
-  SC_LAUNCH(PK_PASS, launch_pass<R>(s, P_STATS, static_cast<const R*>(Rv), static_cast<const R*>(C), nullptr, nullptr, nullptr,
-                         c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, L.tchunk, nullptr, c.st));
-  SC_LAUNCH(PK_REDUCE, launch_station_reduce<R>(s, c.at<R>(L.stat_cost), c.at<R>(L.stat_rho), L.nchunk, w, jones, Jhr,
-                                   c.at<double>(L.H_cur), c.at<double>(L.cpart_cur), nullptr, nullptr, 0.0,
-                                   c.st));
+  int nst = 0;
+  double* stat = c.at<double>(L.lstat);
+  double* part = c.at<double>(L.part);
+  SC_LAUNCH(PK_STATS, launch_lm_stats<R>(s, static_cast<const R*>(Rv), static_cast<const R*>(C), nullptr, stat, &nst,
+                                         c.st));
+  SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, false, stat, nst, jones, part, nullptr, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, jones, Jhr, c.at<double>(L.H_cur), c.at<double>(L.cpart_cur),
+                                          nullptr, nullptr, 0.0, c.st));
   int P = 8 * s.N;
   SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, P, P, w, jones, c.at<double>(L.H_cur), nullptr, static_cast<R*>(JhJ), false, true,
                              c.st));

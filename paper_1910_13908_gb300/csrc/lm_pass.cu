@@ -1,6 +1,7 @@
-// Steps (b) and (c, gradient half): one streaming pass over the visibilities
-// of one cluster, and the per-station reduction that turns its per-baseline
-// sums into J^T r and the 2x2 blocks of J^T J.
+// Step (b): streaming passes over the visibilities of one cluster.  k_pass
+// forms residuals and per-baseline sums: the residual call and its cost, and
+// the running residual of SAGE.  The LM loop works from per-baseline
+// statistics instead (lm_stats.cu).
 //
 // For baseline pq and coherency c = C_pq(t,f) the model is c J_p J_q^H.  The
 // pass forms, per visibility,
@@ -108,9 +109,7 @@ cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, con
   case FL:          \
     return go_pass<R, FL>(s, Xin, C, J_old, J_cur, Rout, stat_cost, stat_rho, nchunk, tchunk, lm, st);
   switch (flags) {
-    SC_PASS(P_OLD | P_SUB | P_STATS)              // LM pass on the running residual
-    SC_PASS(P_SUB | P_STATS)                      // LM pass on explicit data X
-    SC_PASS(P_STATS)                              // gradient sums of a given residual
+    SC_PASS(P_SUB | P_STATS)                      // cost (and per-baseline sums) of a residual
     SC_PASS(P_SUB | P_WRITE_R | P_STATS)          // residual + cost
     SC_PASS(P_SUB | P_WRITE_R)                    // subtract one cluster's model
     SC_PASS(P_OLD | P_SUB | P_WRITE_R)            // replace one cluster's model
@@ -126,8 +125,6 @@ template cudaError_t launch_pass<double>(const Shape&, int, const double*, const
                                          const double*, double*, double*, double*, int, int,
                                          const LMState*, cudaStream_t);
 
-// ---- per-station reduction ---------------------------------------------------------------
-
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -141,105 +138,6 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   }
   return r;  // valid in thread 0
 }
-
-// One block of kReduceThreads threads per station s: lanes stride over the
-// other stations o, form the baseline's contribution in float64 and
-// accumulate in float64; shuffles and one shared-memory step combine the
-// partial sums.  (256 threads per station measured slower than 128.)
-constexpr int kReduceThreads = 128;
-template <typename R>
-__global__ void __launch_bounds__(kReduceThreads) k_station_reduce(int N, int64_t B, int nchunk,
-                                                        const R* __restrict__ stat_cost,
-                                                        const R* __restrict__ stat_rho,
-                                                        const R* __restrict__ w,
-                                                        const double* __restrict__ J,
-                                                        double* __restrict__ g, double* __restrict__ H,
-                                                        double* __restrict__ cpart,
-                                                        const LMState* __restrict__ lm,
-                                                        const double* __restrict__ pen, double pen_w) {
-  if (lm != nullptr && (lm->done | lm->skip)) return;
-  __shared__ double part[kReduceThreads / 32][13];
-  int s = blockIdx.x;
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc[13];
-#pragma unroll
-  for (int i = 0; i < 13; ++i) acc[i] = 0.0;
-  for (int o = threadIdx.x; o < N; o += blockDim.x) {
-    if (o == s) continue;
-    int64_t b = s < o ? bl_index(s, o, N) : bl_index(o, s, N);
-    m22<double> rho = mzero<double>();
-    double cst = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
-      size_t off = (size_t)c * B + b;
-      const R* pr = stat_rho + 8 * off;
-      rho.a.re += pr[0]; rho.a.im += pr[1]; rho.b.re += pr[2]; rho.b.im += pr[3];
-      rho.c.re += pr[4]; rho.c.im += pr[5]; rho.d.re += pr[6]; rho.d.im += pr[7];
-      cst += stat_cost[off];
-    }
-    m22<double> Jo = load_jones<double>(J, o);
-    m22<double> gam = s < o ? mul(rho, Jo) : mul(hconj(rho), Jo);
-    if (s < o) acc[12] += cst;
-    acc[0] += gam.a.re; acc[1] += gam.a.im; acc[2] += gam.b.re; acc[3] += gam.b.im;
-    acc[4] += gam.c.re; acc[5] += gam.c.im; acc[6] += gam.d.re; acc[7] += gam.d.im;
-    double wb = (double)w[b];
-    // w_so J_o^H J_o: (0,0), (1,1) real, (0,1) complex
-    acc[8] += wb * (norm2(Jo.a) + norm2(Jo.c));
-    acc[9] += wb * (norm2(Jo.b) + norm2(Jo.d));
-    cx<double> h01 = cmulc(Jo.a, Jo.b) + cmulc(Jo.c, Jo.d);
-    acc[10] += wb * h01.re;
-    acc[11] += wb * h01.im;
-  }
-#pragma unroll
-  for (int i = 0; i < 13; ++i) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
-    if (lane == 0) part[warp][i] = acc[i];
-  }
-  __syncthreads();
-  if (threadIdx.x < 13) {
-    int i = threadIdx.x;
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < kReduceThreads / 32; ++w) t += part[w][i];
-    if (pen != nullptr) {
-      // quadratic penalty pen_w |theta_s - a_s|^2 as residual rows
-      // sqrt(pen_w) (a - theta): J^T r += pen_w (a - theta), the diagonal of
-      // H (hence of J^T J) += pen_w, cost += pen_w |theta - a|^2
-      const double* a = pen + 8 * s;
-      const double* th = J + 8 * s;
-      if (i < 8) {
-        t += pen_w * (a[i] - th[i]);
-      } else if (i < 10) {
-        t += pen_w;
-      } else if (i == 12) {
-        double e = 0.0;
-        for (int k = 0; k < 8; ++k) e += (th[k] - a[k]) * (th[k] - a[k]);
-        t += pen_w * e;
-      }
-    }
-    if (i < 8) g[8 * s + i] = t;
-    else if (i < 12) H[4 * s + i - 8] = t;
-    else cpart[s] = t;
-  }
-}
-
-template <typename R>
-cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
-                                  int nchunk, const R* w, const double* J, double* g, double* H,
-                                  double* cpart, const LMState* lm, const double* pen, double pen_w,
-                                  cudaStream_t st) {
-  k_station_reduce<R><<<s.N, kReduceThreads, 0, st>>>(s.N, s.B, nchunk, stat_cost, stat_rho, w, J, g, H, cpart, lm,
-                                                      pen, pen_w);
-  return cudaGetLastError();
-}
-template cudaError_t launch_station_reduce<float>(const Shape&, const float*, const float*, int,
-                                                  const float*, const double*, double*, double*,
-                                                  double*, const LMState*, const double*, double,
-                                                  cudaStream_t);
-template cudaError_t launch_station_reduce<double>(const Shape&, const double*, const double*, int,
-                                                   const double*, const double*, double*, double*,
-                                                   double*, const LMState*, const double*, double,
-                                                   cudaStream_t);
 
 __global__ void k_sum_cost(const double* __restrict__ cpart, int N, double* __restrict__ out) {
   __shared__ double sh[32];

@@ -122,58 +122,64 @@ template cudaError_t launch_assemble<double>(const Shape&, int, int, const doubl
 
 // ---- float64 refinement residual r = g - (J^T J + mu I) x ---------------------------------
 
-__device__ __forceinline__ double bsum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[wi] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x < 32) {
-    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-  }
-  return r;
-}
-
 __device__ __forceinline__ m22<double> ld_m22(const double* p) {
   return {{p[0], p[1]}, {p[2], p[3]}, {p[4], p[5]}, {p[6], p[7]}};
 }
 
+// r = g - (J^T J + mu I) x.  With X_s the 2x2 complex form of x's station
+// block and Y_o = X_o^H J_o, the product's station block is
+//     X_s (H_s + mu I) + J_s sum_{o != s} w_so Y_o,
+// so Y is formed once per station (k_refine_prep) and each station then
+// needs 8 multiply-adds per other station: one warp per station, lanes
+// striding over the other stations, a fixed butterfly to combine them.
+__global__ void __launch_bounds__(256) k_refine_prep(int N, const double* __restrict__ J,
+                                                     const double* __restrict__ x,
+                                                     const LMState* __restrict__ lm, double* __restrict__ Y) {
+  if (lm->done | lm->notpd) return;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= N) return;
+  const m22<double> t = h_mul(ld_m22(x + 8 * o), load_jones<double>(J, o));
+  double* y = Y + 8 * o;
+  y[0] = t.a.re, y[1] = t.a.im, y[2] = t.b.re, y[3] = t.b.im;
+  y[4] = t.c.re, y[5] = t.c.im, y[6] = t.d.re, y[7] = t.d.im;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_refine_residual(int N, const R* __restrict__ w,
+__global__ void __launch_bounds__(64) k_refine_residual(int N, const R* __restrict__ w,
                                                          const double* __restrict__ J,
                                                          const double* __restrict__ H,
                                                          const double* __restrict__ g,
                                                          const double* __restrict__ x,
+                                                         const double* __restrict__ Y,
                                                          const LMState* __restrict__ lm,
                                                          double* __restrict__ r) {
-  if (lm->done | lm->skip) return;
-  __shared__ double sh[32];
-  int s = blockIdx.x;
-  // K_s = sum_o w_so dJ_o^H J_o
-  m22<double> K = mzero<double>();
-  for (int o = threadIdx.x; o < N; o += blockDim.x) {
+  if (lm->done | lm->notpd) return;
+  const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (s >= N) return;  // whole warps leave together
+  double k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int o = lane; o < N; o += 32) {
     if (o == s) continue;
-    int64_t b = s < o ? bl_index(s, o, N) : bl_index(o, s, N);
-    double wb = (double)w[b];
-    m22<double> d = ld_m22(x + 8 * o);
-    m22<double> t = h_mul(d, load_jones<double>(J, o));
-    K.a = K.a + scale(t.a, wb); K.b = K.b + scale(t.b, wb);
-    K.c = K.c + scale(t.c, wb); K.d = K.d + scale(t.d, wb);
-  }
-  double k8[8] = {K.a.re, K.a.im, K.b.re, K.b.im, K.c.re, K.c.im, K.d.re, K.d.im};
-  double t8[8];
+    const double wb = (double)w[s < o ? bl_index(s, o, N) : bl_index(o, s, N)];
+    const double2* y = reinterpret_cast<const double2*>(Y + 8 * o);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) t8[i] = bsum(k8[i], sh);
-  if (threadIdx.x == 0) {
-    m22<double> Ks = {{t8[0], t8[1]}, {t8[2], t8[3]}, {t8[4], t8[5]}, {t8[6], t8[7]}};
+    for (int u = 0; u < 4; ++u) {
+      const double2 v = y[u];
+      k[2 * u] = fma(wb, v.x, k[2 * u]);
+      k[2 * u + 1] = fma(wb, v.y, k[2 * u + 1]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) k[u] += __shfl_xor_sync(0xffffffffu, k[u], d);
+  }
+  if (lane == 0) {
+    const m22<double> Ks = {{k[0], k[1]}, {k[2], k[3]}, {k[4], k[5]}, {k[6], k[7]}};
     const double* h = H + 4 * s;
-    double mu = lm->mu;
-    m22<double> Hd = {{h[0] + mu, 0.0}, {h[2], h[3]}, {h[2], -h[3]}, {h[1] + mu, 0.0}};
-    m22<double> ds = ld_m22(x + 8 * s);
-    m22<double> y = mul(ds, Hd) + mul(load_jones<double>(J, s), Ks);
-    double y8[8] = {y.a.re, y.a.im, y.b.re, y.b.im, y.c.re, y.c.im, y.d.re, y.d.im};
+    const double mu = lm->mu;
+    const m22<double> Hd = {{h[0] + mu, 0.0}, {h[2], h[3]}, {h[2], -h[3]}, {h[1] + mu, 0.0}};
+    const m22<double> y = mul(ld_m22(x + 8 * s), Hd) + mul(load_jones<double>(J, s), Ks);
+    const double y8[8] = {y.a.re, y.a.im, y.b.re, y.b.im, y.c.re, y.c.im, y.d.re, y.d.im};
     for (int i = 0; i < 8; ++i) r[8 * s + i] = g[8 * s + i] - y8[i];
   }
 }
@@ -181,15 +187,19 @@ __global__ void __launch_bounds__(256) k_refine_residual(int N, const R* __restr
 template <typename R>
 cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, const double* H,
                                    const double* g, const double* x, const LMState* lm,
-                                   double* r, cudaStream_t st) {
-  k_refine_residual<R><<<s.N, 256, 0, st>>>(s.N, w, J, H, g, x, lm, r);
+                                   double* Y, double* r, cudaStream_t st) {
+  k_refine_prep<<<(s.N + 255) / 256, 256, 0, st>>>(s.N, J, x, lm, Y);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // two stations (warps) per block, so that the float64 work spreads over every SM
+  k_refine_residual<R><<<(s.N + 1) / 2, 64, 0, st>>>(s.N, w, J, H, g, x, Y, lm, r);
   return cudaGetLastError();
 }
 template cudaError_t launch_refine_residual<float>(const Shape&, const float*, const double*,
                                                    const double*, const double*, const double*,
-                                                   const LMState*, double*, cudaStream_t);
+                                                   const LMState*, double*, double*, cudaStream_t);
 template cudaError_t launch_refine_residual<double>(const Shape&, const double*, const double*,
                                                     const double*, const double*, const double*,
-                                                    const LMState*, double*, cudaStream_t);
+                                                    const LMState*, double*, double*, cudaStream_t);
 
 }  // namespace sc

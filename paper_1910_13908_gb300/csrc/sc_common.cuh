@@ -13,6 +13,7 @@ constexpr double kCLight = 299792458.0;
 constexpr int kNB = 64;          // Cholesky tile edge
 constexpr int kCholThreads = 256;
 constexpr int kMaxParts = 4096;  // per-block partial sums of sc_residual_all
+constexpr int kMaxSMs = 512;     // multiprocessor count the workspace layout allows for
 
 // ---- complex scalars -----------------------------------------------------------
 
@@ -168,11 +169,13 @@ struct Workspace {
   // per-solve buffers
   size_t stat_cost;  // [nchunk][B] real
   size_t stat_rho;   // [nchunk][B][8] real
+  size_t lstat;      // [nchunk][10][B] double: per-baseline statistics of an LM solve
+  size_t part;       // per-tile partials of an LM evaluation (double)
   size_t J_old, J_cur, J_trial;  // [8N] double
   size_t g_cur, g_trial;         // [8N] double
   size_t H_cur, H_trial;         // [4N] double
   size_t cpart_cur, cpart_trial; // [N] double
-  size_t x, rvec, corr;          // [Ppad] double
+  size_t x, rvec, ry;            // [Ppad] double (ry: X_o^H J_o of the refinement)
   size_t bvec;                   // [Ppad] solved blocks as tagged 64-bit words (1 per float, 2 per double)
   size_t A;          // [Ppad][Ppad] real
   size_t Linv;       // [nT][64][64] real
@@ -210,6 +213,7 @@ enum ProfKind {
   PK_REFINE,        // float64 refinement residual
   PK_LM,            // LM control
   PK_OTHER,         // small helpers (w sums, cost sums)
+  PK_STATS,         // per-baseline statistics of an LM solve (one pass over the data)
   PK_COUNT
 };
 void prof_start(int kind, cudaStream_t st);
@@ -271,11 +275,24 @@ template <typename R>
 cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, const double* J_old,
                         const double* J_cur, R* Rout, R* stat_cost, R* stat_rho, int nchunk,
                         int tchunk, const LMState* lm, cudaStream_t st);
+// lm_stats.cu: the LM loop from per-baseline statistics.  launch_lm_stats
+// forms, once per solve, S = sum |X|^2, rhoX = sum conj(c) X and
+// W = sum |c|^2 per baseline of the data X = Xin (+ c J_old,p J_old,q^H if
+// J_old is not NULL) into stat [nchunk][10][B]; launch_lm_eval then forms,
+// per LM evaluation at J, the per-tile partials of the cost, J^T r and H
+// (G = J_p J_q^H subtracted if sub, else the residual is X itself), and
+// launch_station_sum adds them into g [8N], H [4N] and the station costs
+// cpart [N], plus the penalty pen_w |theta - pen|^2 if pen is not NULL.
 template <typename R>
-cudaError_t launch_station_reduce(const Shape& s, const R* stat_cost, const R* stat_rho,
-                                  int nchunk, const R* w, const double* J, double* g, double* H,
-                                  double* cpart, const LMState* lm, const double* pen, double pen_w,
-                                  cudaStream_t st);
+cudaError_t launch_lm_stats(const Shape& s, const R* Xin, const R* C, const double* J_old, double* stat,
+                            int* nchunk, cudaStream_t st);
+template <typename R>
+cudaError_t launch_lm_eval(const Shape& s, bool sub, const double* stat, int nchunk, const double* J, double* part,
+                           const LMState* lm, cudaStream_t st);
+cudaError_t launch_station_sum(const Shape& s, const double* part, const double* J, double* g, double* H,
+                               double* cpart, const LMState* lm, const double* pen, double pen_w, cudaStream_t st);
+size_t lm_stats_doubles(int T, int64_t B);  // size of stat for any GPU of at most kMaxSMs SMs
+size_t lm_part_doubles(int N);              // size of the per-tile partials
 cudaError_t launch_sum_cost(const double* cpart, int N, double* out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_sum_reals(const R* x, int64_t n, double* out, cudaStream_t st);
@@ -296,10 +313,11 @@ template <typename R>
 cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const double* J,
                             const double* H, const LMState* lm, R* A, bool damp, bool full,
                             cudaStream_t st);
+// r = g - (J^T J + mu I) x in float64; Y [8N] is scratch
 template <typename R>
 cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, const double* H,
                                    const double* g, const double* x, const LMState* lm,
-                                   double* r, cudaStream_t st);
+                                   double* Y, double* r, cudaStream_t st);
 
 // cholesky.cu
 __host__ __device__ int4 chol_task(int nT, int t);   // (type, i, k, j), type -1 past the end

@@ -269,7 +269,7 @@ def chol_schedule(nT: int, which: int = 0):
 
 
 PROFILE_KINDS = ["station_phasors", "coherency", "vis_pass", "station_reduce", "jhj_assemble",
-                 "cholesky", "tri_solve", "refine_residual", "lm_control", "other"]
+                 "cholesky", "tri_solve", "refine_residual", "lm_control", "other", "lm_stats"]
 
 
 def launch_count() -> int:
