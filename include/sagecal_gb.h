@@ -152,8 +152,21 @@ typedef struct sc_lm_opts {
   int32_t max_ctas;      /* cap on the thread blocks of the persistent
                             factorisation kernel; 0 = enough to fill the GPU.
                             Lower it when several jobs share the device. */
-  int32_t reserved;      /* must be 0 */
+  int32_t chol_kernel;   /* SC_MIXED: which factorisation kernel runs the
+                            64x64 tile products of the bulk,
+                            SC_CHOL_SIMT (0, the default) or SC_CHOL_TENSOR
+                            (1); ignored for SC_FP64 */
 } sc_lm_opts;
+
+/* Factorisation kernels of the float32 path.  SC_CHOL_SIMT: tile products
+ * on the float32 pipes.  SC_CHOL_TENSOR: the TRSM and UPDATE tile products
+ * on the tensor cores (tcgen05, operands staged by TMA, three TF32 passes,
+ * about 2^-21 relative error per product against 2^-24); the diagonal
+ * tiles stay on the float32 pipes.  At the orders of this path the
+ * factorisation is bound by the latency of its task graph, not by
+ * arithmetic, and the SIMT kernel is the faster of the two. */
+#define SC_CHOL_SIMT 0
+#define SC_CHOL_TENSOR 1
 
 typedef struct sc_sage_opts {
   int32_t n_em; /* SAGE/EM sweeps over all clusters */
@@ -320,6 +333,28 @@ SC_API int32_t sc_residual_all(const sc_dims* d, const void* V, const void* C,
                                const double* jones, int32_t corr, void* R,
                                double* cost, int32_t prec, void* ws,
                                size_t ws_bytes, void* stream);
+
+/* Step (c), the dense solve on its own: factorises a symmetric positive
+ * definite matrix as A = L L^T (the factorisation each LM step applies to
+ * the damped J^T J) and solves A x = b by the two triangular substitutions.
+ *   n     order of A, 1 <= n <= 65536
+ *   A     DEVICE in/out, n x n row-major with row pitch lda (>= n) elements,
+ *         float (SC_MIXED) / double (SC_FP64); the lower triangle is read.
+ *         On return the lower triangle holds L; the strict upper triangle is
+ *         unspecified
+ *   b     DEVICE float64 [n], may be NULL (then x is not written)
+ *   x     DEVICE out float64 [n], may equal b
+ *   ws    workspace of at least sc_cholesky_workspace_size() bytes
+ *   chol_kernel  SC_CHOL_SIMT or SC_CHOL_TENSOR (SC_MIXED; ignored for SC_FP64)
+ * The matrix is copied into the workspace, padded to a multiple of 64 with
+ * an identity block, factorised in 64 x 64 tiles and copied back.  A non-positive pivot sets
+ * SC_STATUS_NOTPD in the device status (the call returns SC_OK).
+ * Errors: SC_EINVAL (n, lda, NULL A, unknown kernel), SC_ENOMEM
+ * (workspace), SC_ECUDA. */
+SC_API int32_t sc_cholesky_workspace_size(int32_t n, int32_t prec, size_t* bytes);
+SC_API int32_t sc_cholesky_solve(int32_t n, void* A, int32_t lda, const double* b, double* x,
+                                 int32_t prec, int32_t chol_kernel, void* ws, size_t ws_bytes,
+                                 void* stream);
 
 /* Step (c): Gauss-Newton normal equations of one cluster at residual R
  * (= X - model at `jones`):

@@ -219,7 +219,9 @@ static int check_lm(const sc_lm_opts* o) {
     return fail(SC_EINVAL, "n_lm must be >= 0 and refine_sweeps in [0, 16]");
   if (!(o->tau > 0)) return fail(SC_EINVAL, "tau must be > 0");
   if (!(o->eps_grad >= 0)) return fail(SC_EINVAL, "eps_grad must be >= 0");
-  if (o->max_ctas < 0 || o->reserved != 0) return fail(SC_EINVAL, "max_ctas must be >= 0 and reserved 0");
+  if (o->max_ctas < 0) return fail(SC_EINVAL, "max_ctas must be >= 0");
+  if (o->chol_kernel != SC_CHOL_SIMT && o->chol_kernel != SC_CHOL_TENSOR)
+    return fail(SC_EINVAL, "chol_kernel = %d is neither SC_CHOL_SIMT nor SC_CHOL_TENSOR", o->chol_kernel);
   return SC_OK;
 }
 
@@ -329,7 +331,7 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, H_cur, g_cur, cp_cur, J_cur, J_cur, c.st));
   for (int it = 0; it < o.n_lm; ++it) {
     SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, J_cur, H_cur, lm, A, true, false, c.st));
-    SC_LAUNCH(PK_CHOL, launch_chol<R>(A, L.Ppad, L.nT, Linv, sync, c.status(), lm, o.max_ctas, c.st));
+    SC_LAUNCH(PK_CHOL, launch_chol<R>(A, L.Ppad, L.nT, Linv, sync, c.status(), lm, o.max_ctas, o.chol_kernel, c.st));
     SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, g_cur, bw, x, 0, c.status(), lm, c.st));
     if (mixed) {
       for (int sw = 0; sw < o.refine_sweeps; ++sw) {
@@ -571,6 +573,103 @@ SC_API int32_t sc_lm_normal_eqs(const sc_dims* d, const void* R, const void* C, 
   if (!R || !C || !jones || !JhJ || !Jhr) return fail(SC_EINVAL, "R, C, jones, JhJ and Jhr must not be NULL");
   r = prec == SC_MIXED ? normal_eqs_impl<float>(c, R, C, jones, JhJ, Jhr)
                        : normal_eqs_impl<double>(c, R, C, jones, JhJ, Jhr);
+  return r ? r : ok();
+}
+
+}  // extern "C"
+
+namespace sc {
+
+// Layout of the workspace of sc_cholesky_solve.
+struct CholWs {
+  size_t status, A, Linv, sync, bvec, bpad, xpad, total;
+  int Ppad, nT;
+};
+static CholWs plan_chol_ws(int n, int prec) {
+  CholWs L{};
+  const size_t rs = prec == SC_MIXED ? 4 : 8;
+  L.Ppad = (n + kNB - 1) / kNB * kNB;
+  L.nT = L.Ppad / kNB;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  L.status = take(256);
+  L.A = take((size_t)L.Ppad * L.Ppad * rs);
+  L.Linv = take((size_t)L.nT * kNB * kNB * rs);
+  L.sync = take((size_t)chol_sync_ints(L.nT) * 4);
+  L.bvec = take((size_t)L.Ppad * 2 * rs);
+  L.bpad = take((size_t)L.Ppad * 8);
+  L.xpad = take((size_t)L.Ppad * 8);
+  L.total = o;
+  return L;
+}
+
+template <typename R>
+static int cholesky_impl(int n, R* A, int lda, const double* b, double* x, int kernel, const CholWs& L, char* base,
+                         cudaStream_t st) {
+  R* Aw = reinterpret_cast<R*>(base + L.A);
+  R* Linv = reinterpret_cast<R*>(base + L.Linv);
+  uint32_t* status = reinterpret_cast<uint32_t*>(base + L.status);
+  double* bpad = reinterpret_cast<double*>(base + L.bpad);
+  double* xpad = reinterpret_cast<double*>(base + L.xpad);
+  uint64_t* bw = reinterpret_cast<uint64_t*>(base + L.bvec);
+  int* sync = reinterpret_cast<int*>(base + L.sync);
+  SC_CUDA(cudaMemsetAsync(status, 0, 256, st));
+  // padded copy: A in the leading n x n block, identity beyond it
+  SC_CUDA(cudaMemsetAsync(Aw, 0, (size_t)L.Ppad * L.Ppad * sizeof(R), st));
+  SC_CUDA(cudaMemcpy2DAsync(Aw, (size_t)L.Ppad * sizeof(R), A, (size_t)lda * sizeof(R), (size_t)n * sizeof(R), n,
+                            cudaMemcpyDeviceToDevice, st));
+  SC_CUDA(launch_pad_identity<R>(Aw, L.Ppad, n, st));
+  SC_CUDA(cudaMemsetAsync(sync, 0, (size_t)chol_sync_ints(L.nT) * 4, st));
+  prof_start(PK_CHOL, st);
+  const cudaError_t ce = launch_chol<R>(Aw, L.Ppad, L.nT, Linv, sync, status, nullptr, 0, kernel, st);
+  prof_stop(PK_CHOL, st);
+  SC_CUDA(ce);
+  if (b != nullptr && x != nullptr) {
+    SC_CUDA(cudaMemsetAsync(bpad, 0, (size_t)L.Ppad * 8, st));
+    SC_CUDA(cudaMemcpyAsync(bpad, b, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+    SC_CUDA(cudaMemsetAsync(bw, 0, (size_t)L.Ppad * 2 * sizeof(R), st));
+    prof_start(PK_SOLVE, st);
+    const cudaError_t se = launch_chol_solve<R>(Aw, L.Ppad, L.nT, Linv, sync, bpad, bw, xpad, 0, status, nullptr, st);
+    prof_stop(PK_SOLVE, st);
+    SC_CUDA(se);
+    SC_CUDA(cudaMemcpyAsync(x, xpad, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  SC_CUDA(cudaMemcpy2DAsync(A, (size_t)lda * sizeof(R), Aw, (size_t)L.Ppad * sizeof(R), (size_t)n * sizeof(R), n,
+                            cudaMemcpyDeviceToDevice, st));
+  return SC_OK;
+}
+
+}  // namespace sc
+
+extern "C" {
+
+SC_API int32_t sc_cholesky_workspace_size(int32_t n, int32_t prec, size_t* bytes) {
+  if (n < 1 || n > 65536) return fail(SC_EINVAL, "n = %d outside [1, 65536]", n);
+  if (prec != SC_FP64 && prec != SC_MIXED) return fail(SC_EINVAL, "unknown precision %d", prec);
+  if (!bytes) return fail(SC_EINVAL, "bytes is NULL");
+  *bytes = plan_chol_ws(n, prec).total;
+  return ok();
+}
+
+SC_API int32_t sc_cholesky_solve(int32_t n, void* A, int32_t lda, const double* b, double* x, int32_t prec,
+                                 int32_t chol_kernel, void* ws, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > 65536) return fail(SC_EINVAL, "n = %d outside [1, 65536]", n);
+  if (prec != SC_FP64 && prec != SC_MIXED) return fail(SC_EINVAL, "unknown precision %d", prec);
+  if (chol_kernel != SC_CHOL_SIMT && chol_kernel != SC_CHOL_TENSOR)
+    return fail(SC_EINVAL, "chol_kernel = %d is neither SC_CHOL_SIMT nor SC_CHOL_TENSOR", chol_kernel);
+  if (A == nullptr || lda < n) return fail(SC_EINVAL, "A is NULL or lda = %d < n = %d", lda, n);
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255)) return fail(SC_EINVAL, "workspace NULL or not 256-byte aligned");
+  const CholWs L = plan_chol_ws(n, prec);
+  if (ws_bytes < L.total) return fail(SC_ENOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, L.total);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  const int r = prec == SC_MIXED ? cholesky_impl<float>(n, static_cast<float*>(A), lda, b, x, chol_kernel, L, base, st)
+                                 : cholesky_impl<double>(n, static_cast<double*>(A), lda, b, x, chol_kernel, L, base,
+                                                         st);
   return r ? r : ok();
 }
 

@@ -23,6 +23,9 @@
 // Tiles written by one SM and read by another are moved through L2 only
 // (ld.global.cg / st.global.cg) and published by a release store of the
 // tile's counter, made after the block barrier that follows the stores.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <atomic>
 #include <type_traits>
@@ -479,6 +482,147 @@ __device__ void potrf_tile(R* sm, R* sv, R* aux, int* bad) {
   __syncthreads();
 }
 
+// ---- tensor-core tile products (tcgen05, 3xTF32) ---------------------------------------
+//
+// In float32 the TRSM and UPDATE tiles of the bulk run on the tensor cores.
+// Both products are "NT" (C = X Y^T with X and Y row-major 64x64 tiles, so
+// both operands are K-major): X = A_ij, Y = Linv_jj for TRSM(i, j); X = L_ij,
+// Y = L_kj for UPDATE(i, k, j).  One thread issues two 2-D TMA loads per
+// operand (boxes of 64 rows x 32 floats with the 128-byte swizzle, which is
+// the tensor cores' K-major SW128 layout), completing on an mbarrier.  The
+// block then splits every operand x into x_hi = tf32(x) and x_lo = tf32(x -
+// x_hi) in place, and one thread issues, per step of K = 8, the three
+// products X_lo Y_hi, X_hi Y_lo and X_hi Y_hi (the 3xTF32 scheme, about
+// 2^-21 relative error per product against 2^-24 in float32) into a float32
+// accumulator in tensor memory, then commits to a second mbarrier.  The
+// instruction shape is M = 128, N = 64: the tile fills rows 0..63 and rows
+// 64..127 read the next 8 KB of the operand region, whose results are
+// never read.  Four warps read the accumulator back (tcgen05.ld, one row of
+// 32 columns per thread) and store C (TRSM) or the old tile minus C
+// (UPDATE).  Every mbarrier wait is bounded; a wait that gives up records
+// SC_STATUS_TIMEOUT, and the block still frees its tensor memory.
+namespace tc {
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier (every thread of the block
+// calls it); false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (it >= 8) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// whole warp
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory descriptor of a K-major operand in the 128-byte-swizzled
+// layout: 8-row groups of 128-byte rows 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused by this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+// kind::tf32, float32 accumulator, both operands K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+// 32 consecutive float32 columns of one accumulator row per thread (the
+// warp's lane quadrant), then the wait for the load
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Splits the 64x64 tile at hi (16 KB, any layout) into hi = tf32(x) in place
+// and lo = tf32(x - hi) at lo; the 256 threads take 16-byte vectors.
+__device__ __forceinline__ void split_tile(float* hi, float* lo) {
+  float4* h = reinterpret_cast<float4*>(hi);
+  float4* l = reinterpret_cast<float4*>(lo);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    const float4 x = h[e];
+    const float4 a = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+    h[e] = a;
+    l[e] = make_float4(tf32_rn(x.x - a.x), tf32_rn(x.y - a.y), tf32_rn(x.z - a.z), tf32_rn(x.w - a.w));
+  }
+}
+
+// Operand region: X hi, X lo, Y hi, Y lo, each a 64x64 tile as two K blocks
+// (columns 0..31, 32..63) of 64 rows x 128 bytes.  The M = 128 instruction
+// reads 128 rows of X, so every X block is followed by 8 KB of the region.
+constexpr uint32_t kTile = 64 * 64 * 4;  // 16 KB
+constexpr uint32_t kKBlk = 64 * 128;      // 8 KB
+constexpr uint32_t kOpBytes = 4 * kTile;  // 64 KB
+constexpr uint32_t kTmemCols = 64;
+
+}  // namespace tc
+
 // ---- factorisation ---------------------------------------------------------------------------
 
 // Tasks of the diagonal chain, run by one CTA (the "walker") without flag
@@ -720,6 +864,275 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
   async_wait_all();
 }
 
+
+// The factorisation kernel of the float32 path: the walker as in k_chol; the
+// bulk TRSM/UPDATE tasks on the tensor cores, two deep.  Shared memory holds
+// two stages of raw operands (X, Y: 32 KB each) and one region for the low
+// parts (32 KB).  While the product of the current task runs, the operands
+// of the task claimed next are already arriving by TMA in the other stage,
+// provided that task's dependencies were complete at a non-blocking check;
+// otherwise the block finishes the current task and then waits for them.
+// The lowest unfinished claimed task is always some block's current task,
+// whose dependencies precede it in the list, so list order still rules out
+// deadlock.  Two blocks per SM.
+namespace tc {
+constexpr uint32_t kStage = 2 * kTile;                  // X, Y raw (the high parts after the split)
+constexpr uint32_t kLoOff = 2 * kStage;                 // X lo, Y lo
+constexpr uint32_t kRegion = 2 * kStage + 2 * kTile;    // 96 KB
+}  // namespace tc
+
+__global__ void __launch_bounds__(kCholThreads, 2) k_chol_tc(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmL, float* __restrict__ A,
+                                                        int lda, int nT, float* __restrict__ Linv, int n_tasks,
+                                                        int* sync, uint32_t* status, LMState* lm) {
+  if (lm != nullptr && lm->done) return;
+  extern __shared__ unsigned char smraw[];
+  // 1024-byte alignment of the operand region, whatever precedes the dynamic array
+  const uint32_t raw = tc::saddr(smraw);
+  unsigned char* base = smraw + (((raw + 1023u) & ~1023u) - raw);
+  float* Xl = reinterpret_cast<float*>(base + tc::kLoOff);
+  float* Yl = reinterpret_cast<float*>(base + tc::kLoOff + tc::kTile);
+  uint64_t* bar_load = reinterpret_cast<uint64_t*>(base + tc::kRegion);  // [2], one per stage
+  uint64_t* bar_mma = bar_load + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_load + 3);
+  int* ctl = reinterpret_cast<int*>(bar_load + 4);  // s_task, s_ok, s_bad
+  // the walker's tiles reuse the operand region (padded layout, 3.5 tiles)
+  constexpr int LD = Pitch<float>::value;
+  float* T0 = reinterpret_cast<float*>(base);
+  float* T1 = T0 + kNB * LD;
+  float* T2 = T1 + kNB * LD;
+  float* aux = T2 + kNB * LD;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(bar_load, 1);
+    tc::mbar_init(bar_load + 1, 1);
+    tc::mbar_init(bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, tc::kTmemCols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // phase parities of the mbarriers and which of them have an operation in
+  // flight (the same in every thread: every branch below is block-uniform)
+  uint32_t ph_load[2] = {0, 0}, ph_mma = 0;
+  bool pend_load[2] = {false, false}, pend_mma = false;
+  SyncView sv(sync, nT);
+  int walker_sm = -1, my_sm = 0;
+  if (threadIdx.x == 0) asm volatile("mov.u32 %0, %%smid;" : "=r"(my_sm));
+  auto claim = [&]() -> int {  // thread 0
+    if (walker_sm < 0) {
+      const int w = ld_relaxed(sv.sctr);
+      if (w > 0) walker_sm = w - 1;
+    }
+    return walker_sm == my_sm ? n_tasks : atomicAdd(sv.fctr, 1);
+  };
+  // thread 0: the operands of task tk into stage stg
+  auto issue = [&](int4 tk, int stg) {
+    unsigned char* sb = base + stg * tc::kStage;
+    // the tiles were written by other blocks through the generic proxy and
+    // acquired by this block; make them visible to the copy engine's reads
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    tc::mbar_expect_tx(bar_load + stg, 2 * tc::kTile);
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+      tc::tma_load(sb + kb * tc::kKBlk, &tmA, kNB * tk.w + 32 * kb, kNB * tk.y, bar_load + stg);
+      if (tk.x == T_TRSM)
+        tc::tma_load(sb + tc::kTile + kb * tc::kKBlk, &tmL, 32 * kb, kNB * tk.w, bar_load + stg);
+      else
+        tc::tma_load(sb + tc::kTile + kb * tc::kKBlk, &tmA, kNB * tk.w + 32 * kb, kNB * tk.z, bar_load + stg);
+    }
+  };
+  // epilogue threads: warps 0, 1, 4, 5 read rows 32 (warp % 4) + lane and
+  // columns 32 (warp / 4) .. + 31 of the accumulator
+  const bool epi = (warp & 2) == 0;
+  const int erow = 32 * (warp & 3) + lane, ecol = 32 * (warp >> 2);
+  int next = -1;  // thread 0: the claimed, not yet examined task
+  int4 cur = make_int4(-1, 0, 0, 0);
+  bool have = false;  // cur's operands are on their way into stage stg
+  int stg = 0;
+  bool failed = false;
+  for (;;) {
+    if (!have) {
+      // claim tasks until one is ours, then wait for its dependencies
+      __syncthreads();  // every thread has read the previous ctl[0]
+      if (threadIdx.x == 0) {
+        ctl[0] = next >= 0 ? next : claim();
+        next = -1;
+      }
+      __syncthreads();
+      const int t = ctl[0];
+      if (t >= n_tasks) break;
+      if (t == 0) {
+        if (threadIdx.x == 0) st_release(sv.sctr, my_sm + 1);
+        chol_walker(A, lda, nT, Linv, sv, status, lm, T0, T1, T2, aux, ctl + 2, ctl + 1);
+        break;
+      }
+      cur = chol_task(nT, t);
+      if (walker_task(cur)) continue;
+      if (threadIdx.x == 0) next = claim();
+      bool ok = true;
+      if (threadIdx.x < 3) {
+        const int* p;
+        int v;
+        task_dep(cur, nT, sv, threadIdx.x, p, v);
+        if (p != nullptr) ok = wait_ge(p, v, status);
+      }
+      if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
+        break;
+      }
+      if (threadIdx.x == 0) issue(cur, stg);
+      pend_load[stg] = true;
+      have = true;
+    }
+    // look at the claimed next task; queue its operands if it is ready
+    if (threadIdx.x == 0) ctl[0] = next;
+    __syncthreads();
+    const int t2 = ctl[0];
+    int4 nxt = make_int4(-1, 0, 0, 0);
+    bool staged = false;
+    if (t2 >= 0 && t2 < n_tasks) {
+      nxt = chol_task(nT, t2);
+      if (walker_task(nxt)) {
+        if (threadIdx.x == 0) next = -1;  // done by the walker: skip it
+      } else {
+        bool ready = true;
+        if (threadIdx.x < 3) {
+          const int* p;
+          int v;
+          task_dep(nxt, nT, sv, threadIdx.x, p, v);
+          if (p != nullptr) ready = ld_acquire(p) >= v;
+        }
+        staged = __syncthreads_and(ready) != 0;
+        if (staged && threadIdx.x == 0) {
+          next = claim();
+          issue(nxt, stg ^ 1);
+        }
+        if (staged) pend_load[stg ^ 1] = true;
+      }
+    }
+    // the current task
+    const int i = cur.y, k = cur.z, j = cur.w;
+    const bool trsm = cur.x == T_TRSM;
+    float* Out = A + (size_t)i * kNB * lda + (size_t)(trsm ? j : k) * kNB;
+    float* orow = Out + (size_t)erow * lda + ecol;
+    float old[32];
+    if (epi && !trsm) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(orow) + u);
+        old[4 * u] = v.x, old[4 * u + 1] = v.y, old[4 * u + 2] = v.z, old[4 * u + 3] = v.w;
+      }
+    }
+    const bool landed = tc::mbar_wait(bar_load + stg, ph_load[stg]);
+    if (!__syncthreads_and(landed)) {
+      failed = true;
+      break;
+    }
+    ph_load[stg] ^= 1;
+    pend_load[stg] = false;
+    float* Xh = reinterpret_cast<float*>(base + stg * tc::kStage);
+    float* Yh = reinterpret_cast<float*>(base + stg * tc::kStage + tc::kTile);
+    tc::split_tile(Xh, Xl);
+    tc::split_tile(Yh, Yl);
+    tc::fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after();
+      const uint32_t xh = tc::saddr(Xh), xl = tc::saddr(Xl), yh = tc::saddr(Yh), yl = tc::saddr(Yl);
+#pragma unroll
+      for (int s8 = 0; s8 < 8; ++s8) {  // K = 64 in steps of 8: block s8 / 4, 32 bytes each
+        const uint32_t off = (s8 >> 2) * tc::kKBlk + (s8 & 3) * 32;
+        tc::mma_tf32(tmem, tc::sw128_desc(xl + off), tc::sw128_desc(yh + off), s8 > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, tc::sw128_desc(xh + off), tc::sw128_desc(yl + off), 1u);
+        tc::mma_tf32(tmem, tc::sw128_desc(xh + off), tc::sw128_desc(yh + off), 1u);
+      }
+      tc::mma_commit(bar_mma);
+    }
+    pend_mma = true;
+    const bool done = tc::mbar_wait(bar_mma, ph_mma);
+    if (!__syncthreads_and(done)) {
+      failed = true;
+      break;
+    }
+    ph_mma ^= 1;
+    pend_mma = false;
+    tc::fence_after();
+    if (epi) {
+      float d[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)ecol, d);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        float4 v;
+        if (trsm) v = make_float4(d[4 * u], d[4 * u + 1], d[4 * u + 2], d[4 * u + 3]);
+        else
+          v = make_float4(old[4 * u] - d[4 * u], old[4 * u + 1] - d[4 * u + 1], old[4 * u + 2] - d[4 * u + 2],
+                          old[4 * u + 3] - d[4 * u + 3]);
+        __stcg(reinterpret_cast<float4*>(orow) + u, v);
+      }
+    }
+    tc::fence_before();
+    __syncthreads();  // the tile is stored; the accumulator, the stage and the low parts are free
+    if (threadIdx.x == 32) {
+      if (trsm) st_release(sv.tdone + i * nT + j, 1);
+      else st_release(sv.upd + i * nT + k, j + 1);
+    }
+    if (staged) {
+      cur = nxt;
+      stg ^= 1;
+    } else {
+      have = false;
+    }
+  }
+  // Leave no asynchronous work behind: a stage whose copies were issued and
+  // not consumed, and the product after a wait that gave up, get a bounded
+  // wait before the tensor memory is freed.
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (failed) atomicOr(status, SC_STATUS_TIMEOUT);
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (pend_load[s2]) (void)tc::mbar_wait(bar_load + s2, ph_load[s2]);
+    if (pend_mma) (void)tc::mbar_wait(bar_mma, ph_mma);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, tc::kTmemCols);
+}
+
+// Dynamic shared memory of k_chol_tc: the operand region (which the walker
+// reuses), the mbarriers, the tensor-memory slot and the control words, plus
+// 1 KB for the alignment.
+static size_t chol_tc_smem() { return tc::kRegion + 64 + 1024; }
+
+// Tensor maps of the matrix (rows of lda floats) and of the diagonal-block
+// inverses ([nT * 64] rows of 64 floats): 2-D, boxes of 64 rows x 32 floats,
+// 128-byte swizzle.  cuTensorMapEncodeTiled is reached through the runtime's
+// driver entry point, so the library needs no link to the driver library.
+static cudaError_t encode_tile_map(CUtensorMap* map, const float* base, uint64_t cols, uint64_t rows,
+                                   uint64_t row_bytes) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (encode == nullptr) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {32, 64};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Blocks of the persistent factorisation kernel that fill the GPU (at most
 // 4 per SM).  Computed once per precision; the function-local static makes
 // the first computation thread safe for concurrent callers.
@@ -736,9 +1149,48 @@ static int chol_grid(const void* fn, size_t smem) {
   return cached;
 }
 
+// Blocks of k_chol_tc: two per SM, computed once.  The occupancy query
+// reports one block per SM for a kernel that allocates tensor memory, but
+// registers (112 a thread) and shared memory (97 KB) leave room for two, and
+// two blocks allocate 128 of the 512 tensor-memory columns.  Blocks that do
+// not find a slot start when others leave; tasks are claimed only by running
+// blocks, so nothing waits on a block that has not started.
+static int chol_tc_grid() {
+  static const int cached = [] {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void* fn = reinterpret_cast<const void*>(&k_chol_tc);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_tc_smem());
+    // all of the unified L1 as shared memory: two blocks of ~97 KB per SM
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return std::max(1, 2 * sms);
+  }();
+  return cached;
+}
+
+static cudaError_t launch_chol_tc(float* A, int lda, int nT, float* Linv, int* sync, uint32_t* status, LMState* lm,
+                                  int max_ctas, cudaStream_t st) {
+  const int n_tasks = chol_ntasks(nT);
+  CUtensorMap tmA, tmL;
+  cudaError_t e = encode_tile_map(&tmA, A, (uint64_t)lda, (uint64_t)nT * kNB, (uint64_t)lda * sizeof(float));
+  if (e != cudaSuccess) return e;
+  e = encode_tile_map(&tmL, Linv, kNB, (uint64_t)nT * kNB, kNB * sizeof(float));
+  if (e != cudaSuccess) return e;
+  int grid = std::min(chol_tc_grid(), n_tasks);
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
+  e = cudaMemsetAsync(sync, 0, sizeof(int) * chol_factor_reset_ints(nT), st);
+  if (e != cudaSuccess) return e;
+  k_chol_tc<<<grid, kCholThreads, chol_tc_smem(), st>>>(tmA, tmL, A, lda, nT, Linv, n_tasks, sync, status, lm);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
-                        int max_ctas, cudaStream_t st) {
+                        int max_ctas, int kernel, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (kernel == SC_CHOL_TENSOR) return launch_chol_tc(A, lda, nT, Linv, sync, status, lm, max_ctas, st);
+  }
   int n_tasks = chol_ntasks(nT);
   size_t smem = sizeof(R) * (4 * kNB) * Pitch<R>::value;  // two buffer pairs; the walker uses 3.5 tiles
   const void* fn = reinterpret_cast<const void*>(&k_chol<R>);
@@ -749,9 +1201,9 @@ cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* sta
   k_chol<R><<<grid, kCholThreads, smem, st>>>(A, lda, nT, Linv, n_tasks, sync, status, lm);
   return cudaGetLastError();
 }
-template cudaError_t launch_chol<float>(float*, int, int, float*, int*, uint32_t*, LMState*, int,
+template cudaError_t launch_chol<float>(float*, int, int, float*, int*, uint32_t*, LMState*, int, int,
                                         cudaStream_t);
-template cudaError_t launch_chol<double>(double*, int, int, double*, int*, uint32_t*, LMState*, int,
+template cudaError_t launch_chol<double>(double*, int, int, double*, int*, uint32_t*, LMState*, int, int,
                                          cudaStream_t);
 
 // ---- triangular solves ------------------------------------------------------------------------

@@ -120,6 +120,23 @@ template cudaError_t launch_assemble<double>(const Shape&, int, int, const doubl
                                              const double*, const LMState*, double*, bool, bool,
                                              cudaStream_t);
 
+// Ones on the diagonal of rows n..Ppad-1 of a zeroed padded matrix, so that
+// the padding factorises as the identity.
+template <typename R>
+__global__ void k_pad_identity(R* __restrict__ A, int lda, int n, int Ppad) {
+  const int r = n + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < Ppad) A[(size_t)r * lda + r] = (R)1;
+}
+
+template <typename R>
+cudaError_t launch_pad_identity(R* A, int Ppad, int n, cudaStream_t st) {
+  if (n >= Ppad) return cudaSuccess;
+  k_pad_identity<R><<<1, 64, 0, st>>>(A, Ppad, n, Ppad);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pad_identity<float>(float*, int, int, cudaStream_t);
+template cudaError_t launch_pad_identity<double>(double*, int, int, cudaStream_t);
+
 // ---- float64 refinement residual r = g - (J^T J + mu I) x ---------------------------------
 
 __device__ __forceinline__ m22<double> ld_m22(const double* p) {

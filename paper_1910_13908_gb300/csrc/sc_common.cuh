@@ -319,14 +319,19 @@ cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, 
                                    const double* g, const double* x, const LMState* lm,
                                    double* Y, double* r, cudaStream_t st);
 
+// normal_eqs.cu: identity on rows n..Ppad-1 of a zeroed padded matrix
+template <typename R>
+cudaError_t launch_pad_identity(R* A, int Ppad, int n, cudaStream_t st);
+
 // cholesky.cu
 __host__ __device__ int4 chol_task(int nT, int t);   // (type, i, k, j), type -1 past the end
 __host__ __device__ int4 solve_task(int nT, int t);
 int chol_ntasks(int nT);
 int chol_sync_ints(int nT);
+// kernel: SC_CHOL_SIMT or SC_CHOL_TENSOR (float32 only)
 template <typename R>
 cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
-                        int max_ctas, cudaStream_t st);
+                        int max_ctas, int kernel, cudaStream_t st);
 template <typename R>
 cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* sync,
                               const double* b, uint64_t* bwork, double* x, int accumulate,

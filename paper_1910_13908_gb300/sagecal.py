@@ -25,6 +25,8 @@ SC_FP64 = 0
 SC_MIXED = 1
 
 # device status bits (sc_device_status)
+SC_CHOL_SIMT = 0
+SC_CHOL_TENSOR = 1
 SC_STATUS_NOTPD = 1
 SC_STATUS_TIMEOUT = 2
 SC_STATUS_SINGULAR = 4
@@ -53,7 +55,7 @@ class SkyFullC(_c.Structure):
 class LMOpts(_c.Structure):
     _fields_ = [("n_lm", _c.c_int32), ("refine_sweeps", _c.c_int32),
                 ("tau", _c.c_double), ("eps_grad", _c.c_double),
-                ("max_ctas", _c.c_int32), ("reserved", _c.c_int32)]
+                ("max_ctas", _c.c_int32), ("chol_kernel", _c.c_int32)]
 
 
 class SageOpts(_c.Structure):
@@ -113,6 +115,10 @@ def lib():
         for f in ("sc_graph_capture_sage", "sc_graph_launch", "sc_graph_destroy"):
             getattr(L, f).restype = i32
         L.sc_calibrate_batch.restype = i32
+        L.sc_cholesky_workspace_size.argtypes = [i32, i32, _c.POINTER(sz)]
+        L.sc_cholesky_solve.argtypes = [i32, vp, i32, vp, vp, i32, i32, vp, sz, vp]
+        for f in ("sc_cholesky_workspace_size", "sc_cholesky_solve"):
+            getattr(L, f).restype = i32
         L.sc_launch_count.restype = _c.c_uint64
         L.sc_profile_read.argtypes = [i32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_double)]
         for f in ("sc_profile_begin", "sc_profile_end", "sc_profile_read"):
@@ -383,12 +389,12 @@ def lm_normal_eqs(shape: Shape, R, C, jones, prec: int, ws):
     return JhJ, Jhr
 
 
-def lm_opts(n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, max_ctas=0):
-    return LMOpts(int(n_lm), int(refine_sweeps), float(tau), float(eps_grad), int(max_ctas), 0)
+def lm_opts(n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, max_ctas=0, chol_kernel=0):
+    return LMOpts(int(n_lm), int(refine_sweeps), float(tau), float(eps_grad), int(max_ctas), int(chol_kernel))
 
 
 def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_sweeps=1, tau=1e-3,
-                  eps_grad=1e-12):
+                  eps_grad=1e-12, chol_kernel=0):
     """LM solve of one cluster; `jones` [N][2][2] complex128 is updated in place.
     Returns (jones, cost, iters) with cost/iters device scalars."""
     import torch
@@ -398,15 +404,45 @@ def solve_cluster(shape: Shape, X, C, jones, prec: int, ws, n_lm=10, refine_swee
     _need(jones, torch.complex128, (d.N, 2, 2), "jones")
     cost = torch.zeros((), dtype=torch.float64, device=X.device)
     iters = torch.zeros((), dtype=torch.int32, device=X.device)
-    o = lm_opts(n_lm, refine_sweeps, tau, eps_grad)
+    o = lm_opts(n_lm, refine_sweeps, tau, eps_grad, chol_kernel=chol_kernel)
     dc = d.c()
     _check(lib().sc_solve_cluster(_c.byref(dc), _ptr(X), _ptr(C), _ptr(jones), _c.byref(o),
                                   _ptr(cost), _ptr(iters), prec, _ptr(ws), ws.numel(), _stream()))
     return jones, cost, iters
 
 
+def cholesky_workspace(n: int, prec: int, device="cuda"):
+    import torch
+    nb = _c.c_size_t(0)
+    _check(lib().sc_cholesky_workspace_size(n, prec, _c.byref(nb)))
+    return torch.empty(nb.value, dtype=torch.uint8, device=device)
+
+
+def cholesky_solve(A, b, prec: int, ws=None, chol_kernel=0):
+    """Factorises the SPD matrix A (n x n, float32 for SC_MIXED / float64 for
+    SC_FP64, lower triangle read) in place into L and solves A x = b (b float64
+    [n] or None); chol_kernel SC_CHOL_SIMT / SC_CHOL_TENSOR.  Returns (A
+    holding L in its lower triangle, x)."""
+    import torch
+    n = A.shape[0]
+    rdt = torch.float32 if prec == SC_MIXED else torch.float64
+    _need(A, rdt, (n, A.shape[1]), "A")
+    if A.shape[1] < n or A.stride(1) != 1:
+        raise ValueError("A: expected n x lda row-major with lda >= n")
+    if ws is None:
+        ws = cholesky_workspace(n, prec, A.device)
+    x = None
+    if b is not None:
+        _need(b, torch.float64, (n,), "b")
+        x = torch.empty_like(b)
+    _check(lib().sc_cholesky_solve(n, _ptr(A), A.stride(0), None if b is None else _ptr(b),
+                                   None if x is None else _ptr(x), prec, chol_kernel, _ptr(ws), ws.numel(),
+                                   _stream()))
+    return A, x
+
+
 def calibrate_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, ws, n_em=1,
-                   n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, costs=None, max_ctas=0):
+                   n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, costs=None, max_ctas=0, chol_kernel=0):
     """The whole path for one job; `jones` [K][N][2][2] complex128 is updated in
     place.  Returns (jones, costs [K] device float64)."""
     import torch
@@ -418,7 +454,7 @@ def calibrate_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int
     _need(jones, torch.complex128, (K, d.N, 2, 2), "jones")
     if costs is None:
         costs = torch.zeros((K,), dtype=torch.float64, device=V.device)
-    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas))
+    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas, chol_kernel))
     dc, skc = d.c(), sky.c()
     _check(lib().sc_calibrate_sage(_c.byref(dc), _ptr(uvw), _ptr(freqs), _c.byref(skc), _ptr(V),
                                    _ptr(jones), _c.byref(o), _ptr(costs), prec, _ptr(ws), ws.numel(),

@@ -201,6 +201,23 @@ def test_solve_cluster_full_order_matches_oracle(prec, N, n_lm):
     assert sc.device_status(ws) == 0
 
 
+def test_solve_cluster_full_order_tensor_core_factorisation_matches_oracle():
+    """The mixed-precision LM solve at order 4096 with the tensor-core
+    factorisation kernel (three TF32 passes per tile product, then one more
+    float64 refinement sweep than the float32 kernel needs): the same
+    oracle tolerances as above."""
+    spec, Cs, V, J0, J_ref, cost_ref, it_ref = _full_order_case(512, 3)
+    shp = sc.Shape(512, 1, 1, 1, 100)
+    ws = sc.workspace(shp, sc.SC_MIXED)
+    Jg = tdev(J0, torch.complex128)
+    _, cost, iters = sc.solve_cluster(shp, tdev(V, torch.complex64), tdev(Cs[0], torch.complex64), Jg, sc.SC_MIXED,
+                                      ws, n_lm=3, refine_sweeps=2, eps_grad=0.0, chol_kernel=sc.SC_CHOL_TENSOR)
+    assert iters.item() == it_ref == 3
+    assert abs(cost.item() - cost_ref) <= 1e-4 * cost_ref
+    assert O.aligned_error(Jg.cpu().numpy(), J_ref) <= 1e-4
+    assert sc.device_status(ws) == 0
+
+
 # --- the whole path ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec", PRECS)
