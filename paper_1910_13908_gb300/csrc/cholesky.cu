@@ -592,14 +592,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float tf32_rn(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// x rounded to TF32 (10 explicit mantissa bits), to nearest with ties away
+// from zero, by integer operations on the bit pattern (the conversion
+// instruction is several times slower); exact for the finite values of a
+// positive definite factorisation, which are far from overflow.
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // Splits the 64x64 tile at hi (16 KB, any layout) into hi = tf32(x) in place
-// and lo = tf32(x - hi) at lo; the 256 threads take 16-byte vectors.
+// and lo = x - hi (exact; the tensor core reads its top 19 bits) at lo; the
+// 256 threads take 16-byte vectors.  |x - hi - tf32(lo)| < 2^-21 |x|.
 __device__ __forceinline__ void split_tile(float* hi, float* lo) {
   float4* h = reinterpret_cast<float4*>(hi);
   float4* l = reinterpret_cast<float4*>(lo);
@@ -607,9 +610,9 @@ __device__ __forceinline__ void split_tile(float* hi, float* lo) {
   for (int u = 0; u < 4; ++u) {
     const int e = threadIdx.x + 256 * u;
     const float4 x = h[e];
-    const float4 a = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+    const float4 a = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
     h[e] = a;
-    l[e] = make_float4(tf32_rn(x.x - a.x), tf32_rn(x.y - a.y), tf32_rn(x.z - a.z), tf32_rn(x.w - a.w));
+    l[e] = make_float4(x.x - a.x, x.y - a.y, x.z - a.z, x.w - a.w);
   }
 }
 
