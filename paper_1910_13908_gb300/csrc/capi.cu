@@ -118,6 +118,11 @@ Workspace plan_workspace(const Shape& s, bool job) {
   L.H_trial = take(4 * N * 8);
   L.cpart_cur = take(N * 8);
   L.cpart_trial = take(N * 8);
+  L.gm_cur = take(N * 8);
+  L.gm_trial = take(N * 8);
+  L.pred_part = take((8 * N / 256 + 1) * 8);
+  L.Jf_cur = take(8 * N * 4);
+  L.Jf_trial = take(8 * N * 4);
   L.x = take((size_t)L.Ppad * 8);
   L.rvec = take((size_t)L.Ppad * 8);
   L.ry = take((size_t)L.Ppad * 8);
@@ -299,15 +304,26 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   const Shape& s = c.s;
   const Workspace& L = c.L;
   size_t n8 = (size_t)8 * s.N * sizeof(double);
+  const bool mixed = s.prec == SC_MIXED;
+  LMBufs b{};
+  b.J_cur = c.at<double>(L.J_cur);
+  b.J_trial = c.at<double>(L.J_trial);
+  b.g_cur = c.at<double>(L.g_cur);
+  b.g_trial = c.at<double>(L.g_trial);
+  b.H_cur = c.at<double>(L.H_cur);
+  b.H_trial = c.at<double>(L.H_trial);
+  b.cp_cur = c.at<double>(L.cpart_cur);
+  b.cp_trial = c.at<double>(L.cpart_trial);
+  b.gm_cur = c.at<double>(L.gm_cur);
+  b.gm_trial = c.at<double>(L.gm_trial);
+  b.pred_part = c.at<double>(L.pred_part);
+  b.Jf_cur = mixed ? c.at<float>(L.Jf_cur) : nullptr;
+  b.Jf_trial = mixed ? c.at<float>(L.Jf_trial) : nullptr;
+  // the Jones in the matrix's type for the assembly of J^T J
+  const R* Jr = nullptr;
+  if constexpr (sizeof(R) == 4) Jr = b.Jf_cur;
+  else Jr = b.J_cur;
   double* J_old = c.at<double>(L.J_old);
-  double* J_cur = c.at<double>(L.J_cur);
-  double* J_trial = c.at<double>(L.J_trial);
-  double* g_cur = c.at<double>(L.g_cur);
-  double* g_trial = c.at<double>(L.g_trial);
-  double* H_cur = c.at<double>(L.H_cur);
-  double* H_trial = c.at<double>(L.H_trial);
-  double* cp_cur = c.at<double>(L.cpart_cur);
-  double* cp_trial = c.at<double>(L.cpart_trial);
   double* x = c.at<double>(L.x);
   double* rvec = c.at<double>(L.rvec);
   double* stat = c.at<double>(L.lstat);
@@ -317,35 +333,36 @@ static int lm_solve(const Ctx& c, const R* Xin, bool running, const R* C, const 
   uint64_t* bw = c.at<uint64_t>(L.bvec);
   int* sync = c.at<int>(L.sync);
   LMState* lm = c.lm();
-  const bool mixed = s.prec == SC_MIXED;
 
   SC_CUDA(cudaMemcpyAsync(J_old, J_io, n8, cudaMemcpyDeviceToDevice, c.st));
-  SC_CUDA(cudaMemcpyAsync(J_cur, J_io, n8, cudaMemcpyDeviceToDevice, c.st));
+  SC_CUDA(cudaMemcpyAsync(b.J_cur, J_io, n8, cudaMemcpyDeviceToDevice, c.st));
   SC_CUDA(cudaMemsetAsync(x, 0, (size_t)L.Ppad * sizeof(double), c.st));
   SC_CUDA(cudaMemsetAsync(rvec, 0, (size_t)L.Ppad * sizeof(double), c.st));
   SC_CUDA(cudaMemsetAsync(bw, 0, (size_t)L.Ppad * 2 * sizeof(R), c.st));  // no stale tag can match
   int nst = 0;  // timeslot chunks of the statistics
   SC_LAUNCH(PK_STATS, launch_lm_stats<R>(s, Xin, C, running ? J_old : nullptr, stat, &nst, c.st));
-  SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, nst, J_cur, part, nullptr, c.st));
-  SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, J_cur, g_cur, H_cur, cp_cur, nullptr, pen, pen_w, c.st));
-  SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, H_cur, g_cur, cp_cur, J_cur, J_cur, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, nst, b.J_cur, part, nullptr, c.st));
+  SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, b.J_cur, b.g_cur, b.H_cur, b.cp_cur, b.gm_cur, nullptr, pen, pen_w,
+                                          c.st));
+  SC_LAUNCH(PK_LM, launch_lm_init(lm, &o, s.N, b, b.J_cur, c.st));
   for (int it = 0; it < o.n_lm; ++it) {
-    SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, J_cur, H_cur, lm, A, true, false, c.st));
+    SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, Jr, b.H_cur, lm, A, true, false, c.st));
     SC_LAUNCH(PK_CHOL, launch_chol<R>(A, L.Ppad, L.nT, Linv, sync, c.status(), lm, o.max_ctas, o.chol_kernel, c.st));
-    SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, g_cur, bw, x, 0, c.status(), lm, c.st));
+    SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, b.g_cur, bw, x, 0, c.status(), lm, c.st));
     if (mixed) {
       for (int sw = 0; sw < o.refine_sweeps; ++sw) {
-        SC_LAUNCH(PK_REFINE, launch_refine_residual<R>(s, w, J_cur, H_cur, g_cur, x, lm, c.at<double>(L.ry), rvec,
-                                                       c.st));
+        SC_LAUNCH(PK_REFINE, launch_refine_residual<R>(s, w, b.J_cur, b.H_cur, b.g_cur, x, lm, c.at<double>(L.ry),
+                                                       rvec, c.st));
         SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, rvec, bw, x, 1, c.status(), lm, c.st));
       }
     }
-    SC_LAUNCH(PK_LM, launch_lm_trial(lm, s.N, L.Ppad, J_cur, x, H_cur, g_cur, J_trial, c.st));
-    SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, nst, J_trial, part, lm, c.st));
-    SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, J_trial, g_trial, H_trial, cp_trial, lm, pen, pen_w, c.st));
-    SC_LAUNCH(PK_LM, launch_lm_decide(lm, s.N, cp_trial, J_cur, J_trial, g_cur, g_trial, H_cur, H_trial, c.st));
+    SC_LAUNCH(PK_LM, launch_lm_trial(lm, s.N, x, b, c.st));
+    SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, nst, b.J_trial, part, lm, c.st));
+    SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, b.J_trial, b.g_trial, b.H_trial, b.cp_trial, b.gm_trial, lm, pen,
+                                            pen_w, c.st));
+    SC_LAUNCH(PK_LM, launch_lm_decide(lm, s.N, b, c.st));
   }
-  SC_LAUNCH(PK_LM, launch_lm_finish(lm, J_cur, s.N, J_io, cost_out, iters_out, c.st));
+  SC_LAUNCH(PK_LM, launch_lm_finish(lm, b.J_cur, s.N, J_io, cost_out, iters_out, c.st));
   return SC_OK;
 }
 
@@ -431,10 +448,17 @@ static int normal_eqs_impl(const Ctx& c, const void* Rv, const void* C, const do
                                          c.st));
   SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, false, stat, nst, jones, part, nullptr, c.st));
   SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, jones, Jhr, c.at<double>(L.H_cur), c.at<double>(L.cpart_cur),
-                                          nullptr, nullptr, 0.0, c.st));
+                                          c.at<double>(L.gm_cur), nullptr, nullptr, 0.0, c.st));
   int P = 8 * s.N;
-  SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, P, P, w, jones, c.at<double>(L.H_cur), nullptr, static_cast<R*>(JhJ), false, true,
-                             c.st));
+  const R* Jr = nullptr;
+  if constexpr (sizeof(R) == 4) {
+    SC_LAUNCH(PK_OTHER, launch_round_jones(jones, c.at<float>(L.Jf_cur), 8 * s.N, c.st));
+    Jr = c.at<float>(L.Jf_cur);
+  } else {
+    Jr = jones;
+  }
+  SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, P, P, w, Jr, c.at<double>(L.H_cur), nullptr, static_cast<R*>(JhJ), false,
+                                            true, c.st));
   return SC_OK;
 }
 

@@ -621,7 +621,6 @@ __device__ __forceinline__ void split_tile(float* hi, float* lo) {
 // reads 128 rows of X, so every X block is followed by 8 KB of the region.
 constexpr uint32_t kTile = 64 * 64 * 4;  // 16 KB
 constexpr uint32_t kKBlk = 64 * 128;      // 8 KB
-constexpr uint32_t kOpBytes = 4 * kTile;  // 64 KB
 constexpr uint32_t kTmemCols = 64;
 
 }  // namespace tc

@@ -9,9 +9,19 @@
 //           mu *= nu, nu *= 2; a non-positive-definite factorisation counts
 //           as a rejection.  Every later kernel of the solve returns at once
 //           after the last iteration or the gradient stop.
+//
+// Float64 arithmetic is slow on this GPU, so these kernels keep it to the
+// sums and updates the method needs: the trial step spreads over several
+// blocks (partial predicted decreases, summed in a fixed order by decide),
+// maxima of magnitudes are taken on the bit patterns (integer compares),
+// and the per-station maxima of |J^T r| come from the station sums.  In
+// float32 the trial step also rounds the Jones once for the assembly of
+// J^T J (Jf), so that no later kernel converts them per matrix element.
 #include "sc_common.cuh"
 
 namespace sc {
+
+constexpr int kTrialThreads = 256;
 
 __device__ __forceinline__ double bred_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -24,37 +34,44 @@ __device__ __forceinline__ double bred_sum(double v, double* sh) {
   __syncthreads();
   return r;  // valid in every thread
 }
-__device__ __forceinline__ double bred_max(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+// Maximum of non-negative doubles, compared as their bit patterns (the
+// order of non-negative IEEE doubles is that of their bits).
+__device__ __forceinline__ unsigned long long bred_umax(unsigned long long v, unsigned long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
-  double r = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, sh[i]);
+  unsigned long long r = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = max(r, sh[i]);
   __syncthreads();
   return r;
 }
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
 
-__global__ void k_lm_init(LMState* lm, sc_lm_opts o, int N, const double* __restrict__ H,
-                          const double* __restrict__ g, const double* __restrict__ cpart,
-                          const double* __restrict__ J_src, double* __restrict__ J_cur) {
+__global__ void k_lm_init(LMState* lm, sc_lm_opts o, int N, LMBufs b, const double* __restrict__ J_src) {
   __shared__ double sh[32];
-  double c = 0.0, dmax = 0.0, gmax = 0.0;
+  __shared__ unsigned long long shu[32];
+  double c = 0.0;
+  unsigned long long dmax = 0, gmax = 0;
   for (int s = threadIdx.x; s < N; s += blockDim.x) {
-    c += cpart[s];
-    dmax = fmax(dmax, fmax(H[4 * s], H[4 * s + 1]));
+    c += b.cp_cur[s];
+    dmax = max(dmax, max(abs_bits(b.H_cur[4 * s]), abs_bits(b.H_cur[4 * s + 1])));
+    gmax = max(gmax, abs_bits(b.gm_cur[s]));
   }
   for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) {
-    gmax = fmax(gmax, fabs(g[k]));
-    if (J_src != J_cur) J_cur[k] = J_src[k];
+    const double v = J_src[k];
+    if (J_src != b.J_cur) b.J_cur[k] = v;
+    if (b.Jf_cur != nullptr) b.Jf_cur[k] = (float)v;
   }
   c = bred_sum(c, sh);
-  dmax = bred_max(dmax, sh);
-  gmax = bred_max(gmax, sh);
+  dmax = bred_umax(dmax, shu);
+  gmax = bred_umax(gmax, shu);
   if (threadIdx.x == 0) {
     lm->cost = c;
-    lm->mu = o.tau * dmax;
+    lm->mu = o.tau * __longlong_as_double((long long)dmax);
     lm->nu = 2.0;
     lm->lm_tau = o.tau;
     lm->eps_grad = o.eps_grad;
@@ -66,78 +83,86 @@ __global__ void k_lm_init(LMState* lm, sc_lm_opts o, int N, const double* __rest
     lm->rho = 0.0;
     lm->pred = 0.0;
     lm->cost_trial = 0.0;
-    lm->done = (o.n_lm <= 0 || gmax <= o.eps_grad * (1.0 + c)) ? 1 : 0;
+    lm->done = (o.n_lm <= 0 || __longlong_as_double((long long)gmax) <= o.eps_grad * (1.0 + c)) ? 1 : 0;
   }
 }
 
-cudaError_t launch_lm_init(LMState* lm, const sc_lm_opts* o, int N, const double* H,
-                           const double* g, const double* cpart, const double* J_src,
-                           double* J_cur, cudaStream_t st) {
-  k_lm_init<<<1, 256, 0, st>>>(lm, *o, N, H, g, cpart, J_src, J_cur);
+cudaError_t launch_lm_init(LMState* lm, const sc_lm_opts* o, int N, const LMBufs& b, const double* J_src,
+                           cudaStream_t st) {
+  k_lm_init<<<1, 512, 0, st>>>(lm, *o, N, b, J_src);
   return cudaGetLastError();
 }
 
-__global__ void k_lm_trial(LMState* lm, int N, const double* __restrict__ J_cur,
-                           const double* __restrict__ x, const double* __restrict__ H,
-                           const double* __restrict__ g, double* __restrict__ J_trial) {
+// One thread per parameter: theta_trial = theta + d, and per block the
+// partial predicted decrease sum d (mu d + g).
+__global__ void __launch_bounds__(kTrialThreads) k_lm_trial(LMState* lm, int N, const double* __restrict__ x,
+                                                          LMBufs b) {
   if (lm->done) return;
   __shared__ double sh[32];
   if (lm->notpd) {
-    if (threadIdx.x == 0) lm->skip = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) lm->skip = 1;
     return;
   }
-  double mu = lm->mu, pr = 0.0;
-  for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) {
-    double d = x[k];
-    J_trial[k] = J_cur[k] + d;
-    pr += d * (mu * d + g[k]);
+  const double mu = lm->mu;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double pr = 0.0;
+  if (k < 8 * N) {
+    const double d = x[k];
+    const double jt = b.J_cur[k] + d;
+    b.J_trial[k] = jt;
+    if (b.Jf_trial != nullptr) b.Jf_trial[k] = (float)jt;
+    pr = d * (mu * d + b.g_cur[k]);
   }
   pr = bred_sum(pr, sh);
   if (threadIdx.x == 0) {
-    lm->pred = pr;
-    lm->skip = 0;
+    b.pred_part[blockIdx.x] = pr;
+    if (blockIdx.x == 0) lm->skip = 0;
   }
 }
 
-cudaError_t launch_lm_trial(LMState* lm, int N, int Ppad, const double* J_cur, const double* x,
-                            const double* H, const double* g, double* J_trial, cudaStream_t st) {
-  (void)Ppad;
-  k_lm_trial<<<1, 1024, 0, st>>>(lm, N, J_cur, x, H, g, J_trial);
+int lm_trial_blocks(int N) { return (8 * N + kTrialThreads - 1) / kTrialThreads; }
+
+cudaError_t launch_lm_trial(LMState* lm, int N, const double* x, const LMBufs& b, cudaStream_t st) {
+  k_lm_trial<<<lm_trial_blocks(N), kTrialThreads, 0, st>>>(lm, N, x, b);
   return cudaGetLastError();
 }
 
-__global__ void k_lm_decide(LMState* lm, int N, const double* __restrict__ cpart_trial,
-                            double* __restrict__ J_cur, const double* __restrict__ J_trial,
-                            double* __restrict__ g_cur, const double* __restrict__ g_trial,
-                            double* __restrict__ H_cur, const double* __restrict__ H_trial) {
+__global__ void k_lm_decide(LMState* lm, int N, int n_pred, LMBufs b) {
   if (lm->done) return;
   __shared__ double sh[32];
+  __shared__ unsigned long long shu[32];
   __shared__ int s_accept;
-  bool skipped = lm->skip != 0;
+  const bool skipped = lm->skip != 0;
   double ct = 0.0;
   if (!skipped)
-    for (int s = threadIdx.x; s < N; s += blockDim.x) ct += cpart_trial[s];
+    for (int s = threadIdx.x; s < N; s += blockDim.x) ct += b.cp_trial[s];
   ct = bred_sum(ct, sh);
   if (threadIdx.x == 0) {
+    double pred = 0.0;
+    for (int i = 0; i < n_pred; ++i) pred += b.pred_part[i];
     double rho = -1.0;
-    if (!skipped && lm->pred > 0.0) rho = (lm->cost - ct) / lm->pred;
+    if (!skipped && pred > 0.0) rho = (lm->cost - ct) / pred;
+    lm->pred = skipped ? 0.0 : pred;
     lm->rho = rho;
     lm->cost_trial = ct;
     s_accept = (!skipped && rho > 0.0) ? 1 : 0;
   }
   __syncthreads();
-  int acc = s_accept;
+  const int acc = s_accept;
   if (acc) {
     for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) {
-      J_cur[k] = J_trial[k];
-      g_cur[k] = g_trial[k];
+      b.J_cur[k] = b.J_trial[k];
+      b.g_cur[k] = b.g_trial[k];
+      if (b.Jf_cur != nullptr) b.Jf_cur[k] = b.Jf_trial[k];
     }
-    for (int k = threadIdx.x; k < 4 * N; k += blockDim.x) H_cur[k] = H_trial[k];
+    for (int k = threadIdx.x; k < 4 * N; k += blockDim.x) b.H_cur[k] = b.H_trial[k];
+    for (int s = threadIdx.x; s < N; s += blockDim.x) b.gm_cur[s] = b.gm_trial[s];
   }
-  __syncthreads();
-  double gmax = 0.0;
-  for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) gmax = fmax(gmax, fabs(g_cur[k]));
-  gmax = bred_max(gmax, sh);
+  // the gradient maximum of the state kept: the trial's when accepted
+  const double* gm = acc ? b.gm_trial : b.gm_cur;
+  unsigned long long gmax = 0;
+  for (int s = threadIdx.x; s < N; s += blockDim.x) gmax = max(gmax, abs_bits(gm[s]));
+  gmax = bred_umax(gmax, shu);
   if (threadIdx.x == 0) {
     if (acc) {
       double t = 2.0 * lm->rho - 1.0;
@@ -152,14 +177,13 @@ __global__ void k_lm_decide(LMState* lm, int N, const double* __restrict__ cpart
     lm->iter += 1;
     lm->notpd = 0;
     lm->skip = 0;
-    if (lm->iter >= lm->n_lm || gmax <= lm->eps_grad * (1.0 + lm->cost)) lm->done = 1;
+    if (lm->iter >= lm->n_lm || __longlong_as_double((long long)gmax) <= lm->eps_grad * (1.0 + lm->cost))
+      lm->done = 1;
   }
 }
 
-cudaError_t launch_lm_decide(LMState* lm, int N, const double* cpart_trial, double* J_cur,
-                             const double* J_trial, double* g_cur, const double* g_trial,
-                             double* H_cur, const double* H_trial, cudaStream_t st) {
-  k_lm_decide<<<1, 1024, 0, st>>>(lm, N, cpart_trial, J_cur, J_trial, g_cur, g_trial, H_cur, H_trial);
+cudaError_t launch_lm_decide(LMState* lm, int N, const LMBufs& b, cudaStream_t st) {
+  k_lm_decide<<<1, 512, 0, st>>>(lm, N, lm_trial_blocks(N), b);
   return cudaGetLastError();
 }
 

@@ -283,21 +283,15 @@ static int stats_max_chunks(int T, int64_t B) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(std::min(T, 16), by_size));
 }
 
-// Timeslot chunks of the statistics pass: the count whose (chunk, baseline)
-// items fill the resident threads best (ties within 2% go to fewer chunks).
+// Timeslot chunks of the statistics pass: as few as give at least half as
+// many (chunk, baseline) items as there are resident threads.  Every LM
+// evaluation reads and adds the statistics of every chunk, so a chunk more
+// costs each evaluation 80 bytes per baseline; the pass itself keeps its
+// loads in flight through the ring, not through the number of threads.
 static void stats_chunks(int T, int64_t B, int64_t slots, int* nchunk, int* tchunk) {
-  int best_n = 1;
-  double best_eff = -1.0;
-  const int n_max = stats_max_chunks(T, B);
-  for (int n = 1; n <= n_max; ++n) {
-    const int tc = (T + n - 1) / n, nn = (T + tc - 1) / tc;
-    if (nn != n) continue;
-    const int64_t items = (int64_t)nn * B;
-    const int64_t waves = (items + slots - 1) / slots;
-    const double eff = (double)items / (double)(waves * slots);
-    if (eff > best_eff + 0.02) best_eff = eff, best_n = nn;
-  }
-  *tchunk = (T + best_n - 1) / best_n;
+  const int64_t want = (slots / 2 + std::max<int64_t>(B, 1) - 1) / std::max<int64_t>(B, 1);
+  const int n = (int)std::max<int64_t>(1, std::min<int64_t>(want, stats_max_chunks(T, B)));
+  *tchunk = (T + n - 1) / n;
   *nchunk = (T + *tchunk - 1) / *tchunk;
 }
 
@@ -557,6 +551,7 @@ constexpr int kSumThreads = 64;  // two stations per block: the float64 adds spr
 __global__ void __launch_bounds__(kSumThreads) k_station_sum(int N, int nS, const double* __restrict__ part,
                                                              const double* __restrict__ J, double* __restrict__ g,
                                                              double* __restrict__ H, double* __restrict__ cpart,
+                                                             double* __restrict__ gmax,
                                                              const LMState* __restrict__ lm,
                                                              const double* __restrict__ pen, double pen_w) {
   if (lm != nullptr && (lm->done | lm->skip)) return;
@@ -565,11 +560,22 @@ __global__ void __launch_bounds__(kSumThreads) k_station_sum(int N, int nS, cons
   const int St = s / kST, sl = s % kST;
   const int nrow = nS - St, total = nrow + St + 1;
   const int h = lane >> 4, v = lane & 15;
+  // the partials of this lane, loaded four at a time (independent loads in
+  // flight), added in list order
   double t = 0.0;
   if (v < kRowV) {
-    for (int e = h; e < total; e += 2) {
-      if (e < nrow) t += part[(size_t)tile_pair(St, St + e, nS) * kPartStride + sl * kRowV + v];
-      else if (v < kColV) t += part[(size_t)tile_pair(e - nrow, St, nS) * kPartStride + kST * kRowV + sl * kColV + v];
+    for (int e0 = h; e0 < total; e0 += 8) {
+      double x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 2 * u;
+        x[u] = 0.0;
+        if (e < nrow) x[u] = part[(size_t)tile_pair(St, St + e, nS) * kPartStride + sl * kRowV + v];
+        else if (e < total && v < kColV)
+          x[u] = part[(size_t)tile_pair(e - nrow, St, nS) * kPartStride + kST * kRowV + sl * kColV + v];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t += x[u];
     }
   }
   t += __shfl_down_sync(0xffffffffu, t, 16);
@@ -592,13 +598,19 @@ __global__ void __launch_bounds__(kSumThreads) k_station_sum(int N, int nS, cons
     else if (i < 12) H[4 * s + i - 8] = t;
     else cpart[s] = t;
   }
+  // max_i |g_s,i| over lanes 0..7, compared as bit patterns
+  unsigned long long m = lane < 8 ? ((unsigned long long)__double_as_longlong(t) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && gmax != nullptr) gmax[s] = __longlong_as_double((long long)m);
 }
 
 cudaError_t launch_station_sum(const Shape& s, const double* part, const double* J, double* g, double* H,
-                               double* cpart, const LMState* lm, const double* pen, double pen_w, cudaStream_t st) {
+                               double* cpart, double* gmax, const LMState* lm, const double* pen, double pen_w,
+                               cudaStream_t st) {
   const int nS = (s.N + kST - 1) / kST;
   const unsigned blocks = (unsigned)((s.N + kSumThreads / 32 - 1) / (kSumThreads / 32));
-  k_station_sum<<<blocks, kSumThreads, 0, st>>>(s.N, nS, part, J, g, H, cpart, lm, pen, pen_w);
+  k_station_sum<<<blocks, kSumThreads, 0, st>>>(s.N, nS, part, J, g, H, cpart, gmax, lm, pen, pen_w);
   return cudaGetLastError();
 }
 

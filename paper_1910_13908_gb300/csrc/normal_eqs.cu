@@ -21,9 +21,9 @@
 namespace sc {
 
 template <typename R>
-__device__ __forceinline__ cx<R> jent(const double* __restrict__ J, int s, int i, int j) {
-  const double* p = J + 8 * s + 4 * i + 2 * j;
-  return {(R)p[0], (R)p[1]};
+__device__ __forceinline__ cx<R> jent(const R* __restrict__ J, int s, int i, int j) {
+  const R* p = J + 8 * s + 4 * i + 2 * j;
+  return {p[0], p[1]};
 }
 
 __device__ __forceinline__ void st4(float* d, const float* v) {
@@ -34,9 +34,11 @@ __device__ __forceinline__ void st4(double* d, const double* v) {
   reinterpret_cast<double2*>(d)[1] = make_double2(v[2], v[3]);
 }
 
+// J: the Jones in R (rounded once by the LM trial step in float32), so that
+// the float64 pipe, slow on this GPU, converts nothing per element.
 template <typename R>
 __global__ void __launch_bounds__(256) k_assemble(int N, int lda, int Ppad, const R* __restrict__ w,
-                                                  const double* __restrict__ J,
+                                                  const R* __restrict__ J,
                                                   const double* __restrict__ H,
                                                   const LMState* __restrict__ lm, R* __restrict__ A,
                                                   int damp, int full) {
@@ -46,7 +48,6 @@ __global__ void __launch_bounds__(256) k_assemble(int N, int lda, int Ppad, cons
   int col0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (col0 >= Ppad) return;
   if (!full && col0 > row) return;  // lower triangle (+ the 4-wide group on the diagonal)
-  R mu = (damp && lm != nullptr) ? (R)lm->mu : (R)0;
   R out[4];
   if (row >= P) {
 #pragma unroll
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(256) k_assemble(int N, int lda, int Ppad, cons
         out[u] = v;
       }
     } else {
+      const R mu = (damp && lm != nullptr) ? (R)lm->mu : (R)0;
       const double* h = H + 4 * s;
       int ip = (col0 & 7) >> 2;
 #pragma unroll
@@ -104,8 +106,18 @@ __global__ void __launch_bounds__(256) k_assemble(int N, int lda, int Ppad, cons
   if (col0 < lda) st4(dst, out);
 }
 
+__global__ void k_round_jones(const double* __restrict__ J, float* __restrict__ Jf, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) Jf[k] = (float)J[k];
+}
+
+cudaError_t launch_round_jones(const double* J, float* Jf, int n, cudaStream_t st) {
+  k_round_jones<<<(n + 255) / 256, 256, 0, st>>>(J, Jf, n);
+  return cudaGetLastError();
+}
+
 template <typename R>
-cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const double* J,
+cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const R* J,
                             const double* H, const LMState* lm, R* A, bool damp, bool full,
                             cudaStream_t st) {
   int groups = (Ppad + 3) / 4;
@@ -113,7 +125,7 @@ cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const
   k_assemble<R><<<grd, 128, 0, st>>>(s.N, lda, Ppad, w, J, H, lm, A, damp ? 1 : 0, full ? 1 : 0);
   return cudaGetLastError();
 }
-template cudaError_t launch_assemble<float>(const Shape&, int, int, const float*, const double*,
+template cudaError_t launch_assemble<float>(const Shape&, int, int, const float*, const float*,
                                             const double*, const LMState*, float*, bool, bool,
                                             cudaStream_t);
 template cudaError_t launch_assemble<double>(const Shape&, int, int, const double*, const double*,
@@ -147,8 +159,9 @@ __device__ __forceinline__ m22<double> ld_m22(const double* p) {
 // block and Y_o = X_o^H J_o, the product's station block is
 //     X_s (H_s + mu I) + J_s sum_{o != s} w_so Y_o,
 // so Y is formed once per station (k_refine_prep) and each station then
-// needs 8 multiply-adds per other station: one warp per station, lanes
-// striding over the other stations, a fixed butterfly to combine them.
+// needs 8 multiply-adds per other station: one block of kRefineWarps warps
+// per station, the warps' lanes striding over the other stations, a fixed
+// butterfly within each warp and a fixed-order sum over the warps.
 __global__ void __launch_bounds__(256) k_refine_prep(int N, const double* __restrict__ J,
                                                      const double* __restrict__ x,
                                                      const LMState* __restrict__ lm, double* __restrict__ Y) {
@@ -161,8 +174,9 @@ __global__ void __launch_bounds__(256) k_refine_prep(int N, const double* __rest
   y[4] = t.c.re, y[5] = t.c.im, y[6] = t.d.re, y[7] = t.d.im;
 }
 
+constexpr int kRefineWarps = 4;
 template <typename R>
-__global__ void __launch_bounds__(64) k_refine_residual(int N, const R* __restrict__ w,
+__global__ void __launch_bounds__(32 * kRefineWarps) k_refine_residual(int N, const R* __restrict__ w,
                                                          const double* __restrict__ J,
                                                          const double* __restrict__ H,
                                                          const double* __restrict__ g,
@@ -171,10 +185,10 @@ __global__ void __launch_bounds__(64) k_refine_residual(int N, const R* __restri
                                                          const LMState* __restrict__ lm,
                                                          double* __restrict__ r) {
   if (lm->done | lm->notpd) return;
-  const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (s >= N) return;  // whole warps leave together
+  __shared__ double part[kRefineWarps][8];
+  const int s = blockIdx.x, lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   double k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int o = lane; o < N; o += 32) {
+  for (int o = threadIdx.x; o < N; o += 32 * kRefineWarps) {
     if (o == s) continue;
     const double wb = (double)w[s < o ? bl_index(s, o, N) : bl_index(o, s, N)];
     const double2* y = reinterpret_cast<const double2*>(Y + 8 * o);
@@ -191,6 +205,17 @@ __global__ void __launch_bounds__(64) k_refine_residual(int N, const R* __restri
     for (int d = 16; d > 0; d >>= 1) k[u] += __shfl_xor_sync(0xffffffffu, k[u], d);
   }
   if (lane == 0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) part[wi][u] = k[u];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      double t = part[0][u];
+      for (int v = 1; v < kRefineWarps; ++v) t += part[v][u];
+      k[u] = t;
+    }
     const m22<double> Ks = {{k[0], k[1]}, {k[2], k[3]}, {k[4], k[5]}, {k[6], k[7]}};
     const double* h = H + 4 * s;
     const double mu = lm->mu;
@@ -208,8 +233,7 @@ cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, 
   k_refine_prep<<<(s.N + 255) / 256, 256, 0, st>>>(s.N, J, x, lm, Y);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // two stations (warps) per block, so that the float64 work spreads over every SM
-  k_refine_residual<R><<<(s.N + 1) / 2, 64, 0, st>>>(s.N, w, J, H, g, x, Y, lm, r);
+  k_refine_residual<R><<<s.N, 32 * kRefineWarps, 0, st>>>(s.N, w, J, H, g, x, Y, lm, r);
   return cudaGetLastError();
 }
 template cudaError_t launch_refine_residual<float>(const Shape&, const float*, const double*,

@@ -151,6 +151,16 @@ struct LMState {
   int32_t pad[2];
 };
 
+// Device buffers of one LM solve's state: current and trial Jones,
+// J^T r, diagonal blocks H, station costs and per-station maxima of |J^T r|;
+// the trial step's partial predicted decreases; in float32 the Jones rounded
+// once for the J^T J assembly (NULL in float64).
+struct LMBufs {
+  double *J_cur, *J_trial, *g_cur, *g_trial, *H_cur, *H_trial, *cp_cur, *cp_trial, *gm_cur, *gm_trial;
+  double* pred_part;
+  float *Jf_cur, *Jf_trial;
+};
+
 // ---- workspace ------------------------------------------------------------------------
 
 // Offsets of every scratch buffer inside the caller's workspace.
@@ -175,6 +185,9 @@ struct Workspace {
   size_t g_cur, g_trial;         // [8N] double
   size_t H_cur, H_trial;         // [4N] double
   size_t cpart_cur, cpart_trial; // [N] double
+  size_t gm_cur, gm_trial;       // [N] double, max_i |J^T r| of each station
+  size_t pred_part;              // [8N / 256 + 1] double, partial predicted decreases
+  size_t Jf_cur, Jf_trial;       // [8N] float, the Jones rounded for the float32 assembly
   size_t x, rvec, ry;            // [Ppad] double (ry: X_o^H J_o of the refinement)
   size_t bvec;                   // [Ppad] solved blocks as tagged 64-bit words (1 per float, 2 per double)
   size_t A;          // [Ppad][Ppad] real
@@ -282,7 +295,8 @@ cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, con
 // per LM evaluation at J, the per-tile partials of the cost, J^T r and H
 // (G = J_p J_q^H subtracted if sub, else the residual is X itself), and
 // launch_station_sum adds them into g [8N], H [4N] and the station costs
-// cpart [N], plus the penalty pen_w |theta - pen|^2 if pen is not NULL.
+// cpart [N] (and the per-station maxima of |J^T r|, gmax [N]), plus the
+// penalty pen_w |theta - pen|^2 if pen is not NULL.
 template <typename R>
 cudaError_t launch_lm_stats(const Shape& s, const R* Xin, const R* C, const double* J_old, double* stat,
                             int* nchunk, cudaStream_t st);
@@ -290,7 +304,8 @@ template <typename R>
 cudaError_t launch_lm_eval(const Shape& s, bool sub, const double* stat, int nchunk, const double* J, double* part,
                            const LMState* lm, cudaStream_t st);
 cudaError_t launch_station_sum(const Shape& s, const double* part, const double* J, double* g, double* H,
-                               double* cpart, const LMState* lm, const double* pen, double pen_w, cudaStream_t st);
+                               double* cpart, double* gmax, const LMState* lm, const double* pen, double pen_w,
+                               cudaStream_t st);
 size_t lm_stats_doubles(int T, int64_t B);  // size of stat for any GPU of at most kMaxSMs SMs
 size_t lm_part_doubles(int N);              // size of the per-tile partials
 cudaError_t launch_sum_cost(const double* cpart, int N, double* out, cudaStream_t st);
@@ -309,10 +324,12 @@ cudaError_t launch_residual_all(const Shape& s, const R* V, const R* C, const R*
                                 cudaStream_t st);
 
 // normal_eqs.cu
+// J: the Jones in the matrix's type (rounded once in float32)
 template <typename R>
-cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const double* J,
+cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const R* J,
                             const double* H, const LMState* lm, R* A, bool damp, bool full,
                             cudaStream_t st);
+cudaError_t launch_round_jones(const double* J, float* Jf, int n, cudaStream_t st);
 // r = g - (J^T J + mu I) x in float64; Y [8N] is scratch
 template <typename R>
 cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, const double* H,
@@ -338,14 +355,11 @@ cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* s
                               uint32_t* status, const LMState* lm, cudaStream_t st);
 
 // lm_control.cu
-cudaError_t launch_lm_init(LMState* lm, const sc_lm_opts* o, int N, const double* H,
-                           const double* g, const double* cpart, const double* J_src,
-                           double* J_cur, cudaStream_t st);
-cudaError_t launch_lm_trial(LMState* lm, int N, int Ppad, const double* J_cur, const double* x,
-                            const double* H, const double* g, double* J_trial, cudaStream_t st);
-cudaError_t launch_lm_decide(LMState* lm, int N, const double* cpart_trial, double* J_cur,
-                             const double* J_trial, double* g_cur, const double* g_trial,
-                             double* H_cur, const double* H_trial, cudaStream_t st);
+cudaError_t launch_lm_init(LMState* lm, const sc_lm_opts* o, int N, const LMBufs& b, const double* J_src,
+                           cudaStream_t st);
+cudaError_t launch_lm_trial(LMState* lm, int N, const double* x, const LMBufs& b, cudaStream_t st);
+int lm_trial_blocks(int N);
+cudaError_t launch_lm_decide(LMState* lm, int N, const LMBufs& b, cudaStream_t st);
 cudaError_t launch_lm_finish(const LMState* lm, const double* J_cur, int N, double* J_out,
                              double* cost_out, int32_t* iters_out, cudaStream_t st);
 
