@@ -496,10 +496,17 @@ typedef struct sc_consensus_opts {
  *   Z        DEVICE out complex128 [K][n_poly][N][2][2], the frequency model
  *   costs    DEVICE out float64 [n_bands][K], final LM cost of each cluster
  *            in the last iteration, penalty included; may be NULL
- * The bands run one after another on `stream`, sharing the workspace
- * (sc_workspace_size of d).  Errors as sc_calibrate_sage; SC_EINVAL also for
- * n_bands, n_poly, n_admm or rho out of range.  A singular B^T B raises
- * SC_STATUS_BASIS and zeroes Z. */
+ * Workspace: m = ws_bytes / W whole band workspaces, W = sc_workspace_size
+ * of d rounded up to 256 bytes (m >= 1).  The J-steps of min(m, n_bands,
+ * 16) bands run at once, each band f on internal stream f mod m with band
+ * workspace f mod m, joined back to `stream` before each Z-step (events, so
+ * a capture of `stream` captures them too); with m = 1 they run one after
+ * another on `stream`.  The persistent factorisation of each concurrent
+ * band is capped at 2 x SMs / m thread blocks unless lm.max_ctas is set.
+ * The result does not depend on m.  The device status at offset 0 of ws
+ * gathers every band workspace's status.  Errors as sc_calibrate_sage;
+ * SC_EINVAL also for n_bands, n_poly, n_admm or rho out of range.  A
+ * singular B^T B raises SC_STATUS_BASIS and zeroes Z. */
 SC_API int32_t sc_calibrate_consensus(const sc_dims* d, int32_t n_bands, const double* uvw,
                                       const double* freqs, const sc_sky* sky, const void* V,
                                       const double* basis, double* jones, double* dual, double* Z,

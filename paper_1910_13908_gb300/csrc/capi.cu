@@ -10,6 +10,7 @@
 #include <vector>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "sc_common.cuh"
@@ -462,6 +463,36 @@ static int normal_eqs_impl(const Ctx& c, const void* Rv, const void* C, const do
   return SC_OK;
 }
 
+// Internal streams and events for the concurrent bands of the consensus
+// call, created once per device and kept for the life of the process.
+constexpr int kConsensusStreams = 16;
+static int consensus_streams(int m, cudaStream_t* st, cudaEvent_t* fork, cudaEvent_t* joins) {
+  constexpr int kDevs = 64;
+  struct Pool {
+    cudaStream_t s[kConsensusStreams];
+    cudaEvent_t fork, join[kConsensusStreams];
+    bool made;
+  };
+  static Pool pools[kDevs];
+  static std::mutex mu;
+  int dev = 0;
+  SC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kDevs) return fail(SC_ECUDA, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(mu);
+  Pool& p = pools[dev];
+  if (!p.made) {
+    for (int k = 0; k < kConsensusStreams; ++k) {
+      SC_CUDA(cudaStreamCreateWithFlags(&p.s[k], cudaStreamNonBlocking));
+      SC_CUDA(cudaEventCreateWithFlags(&p.join[k], cudaEventDisableTiming));
+    }
+    SC_CUDA(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
+    p.made = true;
+  }
+  for (int k = 0; k < m; ++k) st[k] = p.s[k], joins[k] = p.join[k];
+  *fork = p.fork;
+  return SC_OK;
+}
+
 }  // namespace sc
 
 using namespace sc;
@@ -876,27 +907,57 @@ SC_API int32_t sc_calibrate_consensus(const sc_dims* d, int32_t n_bands, const d
   const size_t rs = prec == SC_MIXED ? 4 : 8;
   const size_t v_band = (size_t)s.T * s.B * s.F * 8 * rs;  // bytes of one band's data
   const size_t j_band = (size_t)K * P;                      // doubles of one band's Jones
-  double* target = c.at<double>(c.L.pen);
   const double pen_w = 0.5 * opts->rho;
+  // band workspaces: as many whole ones as ws holds, at most one per band
+  const size_t per = align256(c.L.total);
+  const int m = (int)std::max<size_t>(1, std::min<size_t>({ws_bytes / per, (size_t)n_bands, (size_t)kConsensusStreams}));
+  cudaStream_t streams[kConsensusStreams];
+  cudaEvent_t fork = nullptr, joins[kConsensusStreams];
+  sc_sage_opts so = opts->sage;
+  if (m > 1) {
+    if ((r = consensus_streams(m, streams, &fork, joins))) return r;
+    if (so.lm.max_ctas == 0) so.lm.max_ctas = std::max(8, 2 * device_sms() / m);
+  }
+  std::vector<Ctx> band(m, c);
+  for (int k = 1; k < m; ++k) {
+    band[k].base = c.base + per * k;
+    SC_CUDA(cudaMemsetAsync(band[k].status(), 0, 256, c.st));
+  }
   for (int it = 0; it < opts->n_admm; ++it) {
+    if (m > 1) {
+      SC_CUDA(cudaEventRecord(fork, c.st));
+      for (int k = 0; k < m; ++k) {
+        SC_CUDA(cudaStreamWaitEvent(streams[k], fork, 0));
+        band[k].st = streams[k];
+      }
+    }
     for (int f = 0; f < n_bands; ++f) {
+      const Ctx& cb = band[f % m];
+      double* target = cb.at<double>(cb.L.pen);
       const double* pen = nullptr;
       if (it > 0) {
-        SC_LAUNCH(PK_OTHER, launch_consensus_target(f, n_poly, K, P, basis, Z, dual, target, c.st));
+        SC_CUDA(launch_consensus_target(f, n_poly, K, P, basis, Z, dual, target, cb.st));
         pen = target;
       }
       const void* Vf = static_cast<const char*>(V) + v_band * f;
       double* cf = costs ? costs + (size_t)K * f : nullptr;
       r = prec == SC_MIXED
-              ? sage<float>(c, uvw, freqs + (size_t)s.F * f, sky, static_cast<const float*>(Vf),
-                            jones + j_band * f, opts->sage, cf, pen, pen_w)
-              : sage<double>(c, uvw, freqs + (size_t)s.F * f, sky, static_cast<const double*>(Vf),
-                             jones + j_band * f, opts->sage, cf, pen, pen_w);
+              ? sage<float>(cb, uvw, freqs + (size_t)s.F * f, sky, static_cast<const float*>(Vf), jones + j_band * f,
+                            so, cf, pen, pen_w)
+              : sage<double>(cb, uvw, freqs + (size_t)s.F * f, sky, static_cast<const double*>(Vf),
+                             jones + j_band * f, so, cf, pen, pen_w);
       if (r) return r;
+    }
+    if (m > 1) {
+      for (int k = 0; k < m; ++k) {
+        SC_CUDA(cudaEventRecord(joins[k], streams[k]));
+        SC_CUDA(cudaStreamWaitEvent(c.st, joins[k], 0));
+      }
     }
     SC_LAUNCH(PK_OTHER, launch_consensus_fit(n_bands, n_poly, K, P, basis, jones, dual, Z, c.status(), c.st));
     SC_LAUNCH(PK_OTHER, launch_consensus_dual(n_bands, n_poly, K, P, basis, jones, Z, dual, c.st));
   }
+  for (int k = 1; k < m; ++k) SC_LAUNCH(PK_OTHER, launch_or_status(band[k].status(), c.status(), c.st));
   return ok();
 }
 

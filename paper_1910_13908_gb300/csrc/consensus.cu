@@ -147,4 +147,14 @@ cudaError_t launch_consensus_dual(int n_bands, int n_poly, int K, int P, const d
   return cudaGetLastError();
 }
 
+// Adds the device status word of a band workspace to the call's.
+__global__ void k_or_status(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst) {
+  if (threadIdx.x == 0 && *src != 0) atomicOr(dst, *src);
+}
+
+cudaError_t launch_or_status(const uint32_t* src, uint32_t* dst, cudaStream_t st) {
+  k_or_status<<<1, 32, 0, st>>>(src, dst);
+  return cudaGetLastError();
+}
+
 }  // namespace sc

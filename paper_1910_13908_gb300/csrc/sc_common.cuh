@@ -258,6 +258,7 @@ cudaError_t launch_consensus_target(int band, int n_poly, int K, int P, const do
                                     const double* Z, const double* U, double* target, cudaStream_t st);
 cudaError_t launch_consensus_dual(int n_bands, int n_poly, int K, int P, const double* basis,
                                   const double* J, const double* Z, double* U, cudaStream_t st);
+cudaError_t launch_or_status(const uint32_t* src, uint32_t* dst, cudaStream_t st);
 
 // predict_full.cu
 cudaError_t launch_source_params(const Shape& s, int S, const double* freqs, const SkyFull& k, float4* st,

@@ -543,6 +543,15 @@ def capture_sage(shape: Shape, uvw, freqs, sky: DeviceSky, V, jones, prec: int, 
     return Graph(h, (uvw, freqs, sky, V, jones, costs, ws))
 
 
+def consensus_workspace(shape: Shape, prec: int, concurrent: int = 1, device="cuda"):
+    """Workspace of sc_calibrate_consensus for `concurrent` bands at once:
+    that many whole band workspaces (each sc_workspace_size rounded up to
+    256 bytes)."""
+    import torch
+    per = (workspace_size(shape, prec) + 255) // 256 * 256
+    return torch.empty(per * max(1, int(concurrent)), dtype=torch.uint8, device=device)
+
+
 def calibrate_consensus(shape: Shape, uvw, freqs, sky: DeviceSky, V, basis, jones, prec: int, ws, rho,
                         n_admm=3, n_em=1, n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12, max_ctas=0,
                         dual=None):

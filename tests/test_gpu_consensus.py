@@ -45,10 +45,10 @@ def bands(N, n_bands=4, T=2, F=2, K=2, S=3, sigma=0.05, seed=7):
     return spec, uvw, fr, centres, sky, Vs, Css, Jt
 
 
-def run_gpu(prec, spec, uvw, fr, sky, Vs, basis, J0, rho, n_admm, n_em, n_lm):
+def run_gpu(prec, spec, uvw, fr, sky, Vs, basis, J0, rho, n_admm, n_em, n_lm, concurrent=1):
     cdt = torch.complex64 if prec == sc.SC_MIXED else torch.complex128
     shp = sc.Shape(spec.N, spec.T, spec.F, spec.K, spec.S)
-    ws = sc.workspace(shp, prec)
+    ws = sc.consensus_workspace(shp, prec, concurrent)
     J = tdev(J0, torch.complex128)
     _, U, Z, costs = sc.calibrate_consensus(shp, tdev(uvw, torch.float64), tdev(fr, torch.float64),
                                             sc.DeviceSky.from_synth(sky), tdev(np.stack(Vs), cdt),
@@ -120,3 +120,18 @@ def test_singular_basis_is_flagged():
     J, U, Z, costs, status = run_gpu(sc.SC_MIXED, spec, uvw, fr, sky, Vs, basis, J0, 10.0, 2, 1, 3)
     assert status & sc.SC_STATUS_BASIS
     assert np.all(Z == 0)
+
+
+@pytest.mark.parametrize("prec", [sc.SC_FP64, sc.SC_MIXED])
+def test_concurrent_bands_equal_sequential_bands(prec):
+    """A workspace for four bands runs the four J-steps at once on internal
+    streams; every output equals the sequential run's bit for bit (each
+    band's kernels are deterministic and see the same inputs)."""
+    spec, uvw, fr, centres, sky, Vs, Css, Jt = bands(20)
+    basis = synth.frequency_basis(centres, 2)
+    J0 = np.broadcast_to(np.eye(2, dtype=complex), (4, spec.K, spec.N, 2, 2)).copy()
+    seq = run_gpu(prec, spec, uvw, fr, sky, Vs, basis, J0, 5.0, 2, 1, 4, concurrent=1)
+    par = run_gpu(prec, spec, uvw, fr, sky, Vs, basis, J0, 5.0, 2, 1, 4, concurrent=4)
+    for a, b in zip(seq[:4], par[:4]):
+        assert np.array_equal(a, b)
+    assert seq[4] == par[4] == 0
