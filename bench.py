@@ -49,6 +49,10 @@ WORKLOADS = {
                                   "(spectral index -0.7), 10 clusters x 25 sources, 3 SAGE sweeps x 10 LM"),
     "lofar64": ("c1", 1, 10, "64 stations (2016 baselines), 10 timeslots, 1 channel at 150 MHz, "
                              "1 cluster x 20 sources, 10 LM"),
+    "consensus16": ("consensus", 1, 10, "16 sub-bands tiling 115-185 MHz, each 128 stations (8128 baselines), "
+                                        "10 timeslots, 2 channels, 10 clusters x 25 sources; Jones drifting "
+                                        "linearly across the band; consensus ADMM on a 3-term frequency model, "
+                                        "3 iterations of 1 SAGE sweep x 10 LM per band"),
     "serve500": ("c5", 3, 10, "Poisson-arriving calibration jobs: stations uniform in {64,128,256,384,512}, "
                               "clusters 1-40 x 25 sources, 5-20 timeslots, 1-8 channels 140-160 MHz, 3 SAGE "
                               "sweeps x 10 LM, continuous batching with HBM-footprint admission"),
@@ -807,14 +811,23 @@ def serve_spec(i, seed=0):
 def host_job_from_gpu(i, spec, prec, dev):
     """Host arrays of one serving job; its visibilities are simulated on the
     GPU with the library's prediction (an input, not a result)."""
-    from paper_1910_13908_gb300 import serve
+    return staged_to_host(stage_job(i, spec, prec, dev))
+
+
+def stage_job(i, spec, prec, dev):
+    """One serving job's inputs, simulated on the device and kept there until
+    the job arrives (no GPU work left for the arrival itself)."""
     job = make_job(spec, prec, dev)
-    sky = job["sky_host"]
-    V = job["V"].cpu().numpy()
-    hj = serve.HostJob(i, sc_shape(spec), synth.station_uvw(spec), synth.freqs(spec), sky.l, sky.m, sky.flux,
-                       sky.alpha, [int(x) for x in sky.offsets], V, synth.identity_jones(spec.K, spec.N))
-    del job
-    return hj
+    return dict(i=i, spec=spec, V=job["V"], sky=job["sky_host"])
+
+
+def staged_to_host(st):
+    """The job as it arrives: host arrays (the device copy of V is dropped)."""
+    from paper_1910_13908_gb300 import serve
+    spec, sky = st["spec"], st["sky"]
+    V = st.pop("V").cpu().numpy()
+    return serve.HostJob(st["i"], sc_shape(spec), synth.station_uvw(spec), synth.freqs(spec), sky.l, sky.m,
+                         sky.flux, sky.alpha, [int(x) for x in sky.offsets], V, synth.identity_jones(spec.K, spec.N))
 
 
 def sc_shape(spec):
@@ -833,27 +846,41 @@ def run_serve(args, rank, world, local_rank):
     prec = sc.SC_FP64 if args.prec == "fp64" else sc.SC_MIXED
     n_jobs = args.jobs
     specs = [serve_spec(i, seed=rank) for i in range(n_jobs)]
-    # single-stream capacity: a few jobs, one at a time
-    probe = serve.Server(prec=prec, max_slots=1, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
-    probe.start()
-    taus = []
-    for i in range(min(4, n_jobs)):
-        hj = host_job_from_gpu(100000 + i, specs[i], prec, dev)
-        t0 = time.perf_counter()
-        probe.submit(hj)
-        probe.drain()
-        taus.append(time.perf_counter() - t0)
-    probe.close()
-    tau = float(np.mean(taus))
-    rate = args.rate if args.rate > 0 else 0.8 / tau
-    # producer: host data of upcoming jobs, a few ahead
+    def work(sp):                                     # vis.cluster.iter of one job (a spec or a shape)
+        return sp.N * (sp.N - 1) // 2 * sp.T * sp.F * sp.K * n_lm * n_em
+
+    # capacity of the server: a probe of 48 jobs drawn from the same mix
+    # (other seeds), all submitted at once, measured in work per second (the
+    # probe's jobs are not the run's, so jobs/s would carry their size)
+    def capacity(slots, jobs):
+        srv = serve.Server(prec=prec, max_slots=slots, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
+        srv.start()
+        for hj in jobs:
+            srv.submit(hj)
+        srv.drain()
+        span = srv.stats()["span_s"]
+        srv.close()
+        return sum(work(hj.shape) for hj in jobs) / span
+
+    n_probe = min(48, n_jobs)
+    probe_jobs = [host_job_from_gpu(100000 + i, serve_spec(100000 + i, seed=rank), prec, dev) for i in range(n_probe)]
+    cap_single = capacity(1, probe_jobs)              # one job at a time
+    cap_slots = capacity(args.slots, probe_jobs)      # the server's own overlap
+    del probe_jobs
+    mean_work = float(np.mean([work(sp) for sp in specs]))
+    rate = args.rate if args.rate > 0 else 0.8 * cap_single / mean_work
+    # every job's inputs are simulated on the device before the run (no
+    # simulation competes with the server); a producer thread only copies
+    # the next few jobs to the host ahead of their arrival
+    staged = [stage_job(i, sp, prec, dev) for i, sp in enumerate(specs)]
+    torch.cuda.synchronize(dev)
     q = queue.Queue(maxsize=8)
 
     def produce():
         s = torch.cuda.Stream(dev)
         with torch.cuda.stream(s):
-            for i, sp in enumerate(specs):
-                q.put(host_job_from_gpu(i, sp, prec, dev))
+            for i in range(n_jobs):
+                q.put(staged_to_host(staged[i]))
     th = threading.Thread(target=produce, daemon=True)
     th.start()
     u = synth.uniform(rank, synth.TAG_JOBS + 3, n_jobs)
@@ -873,20 +900,144 @@ def run_serve(args, rank, world, local_rank):
     st = srv.stats()
     n_launch = sc.launch_count() - n0
     clk = clocks.stop()
+    # where the latency goes: waiting for admission (queueing) against being
+    # on the device (service), and the tail by job size
+    done = [(srv.results[j], specs[j]) for j in sorted(srv.results) if srv.results[j].outcome == "done"]
+    wait = np.array([r.admitted - r.arrival for r, _ in done])
+    service = np.array([r.finished - r.admitted for r, _ in done])
+    lat = wait + service
+    wjob = np.array([work(sp) for _, sp in done], dtype=np.float64)
+    tail = lat >= np.percentile(lat, 95)
+    breakdown = {
+        "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "service_s": {"p50": float(np.percentile(service, 50)), "p99": float(np.percentile(service, 99))},
+        "tail_5pct": {"mean_queue_wait_s": float(wait[tail].mean()), "mean_service_s": float(service[tail].mean()),
+                      "mean_work_vs_median_job": float(wjob[tail].mean() / np.median(wjob)),
+                      "stations": sorted(int(sp.N) for (r, sp), t in zip(done, tail) if t)},
+        "latency_by_stations_p50_s": {str(n): float(np.median(lat[[sp.N == n for _, sp in done]]))
+                                      for n in (64, 128, 256, 384, 512)
+                                      if any(sp.N == n for _, sp in done)},
+    }
     srv.close()
-    units = sum(sp.B * sp.T * sp.F * sp.K * n_lm * n_em for sp in specs)
+    units = sum(work(sp) for sp in specs)
     value = units / st["span_s"]
     line = {
         "metric": METRIC + "; serving p50/p99 solve latency", "value": value, "unit": UNIT, "n_gpus": world,
         "steps": 1, "warmup": 0, "ms_per_step": 1e3 * st["span_s"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == sc.SC_MIXED else "f64", "data": "synthetic",
         "config": {"workload": "serve500", "description": desc, "jobs": n_jobs, "slots": args.slots,
-                   "arrival_rate_hz": rate, "single_stream_job_s": tau,
-                   "rate_rule": "0.8 x measured single-stream capacity" if args.rate <= 0 else "given"},
+                   "arrival_rate_hz": rate, "mean_job_work": mean_work,
+                   "capacity_single_stream": cap_single, "capacity_%d_slots" % args.slots: cap_slots,
+                   "capacity_unit": UNIT,
+                   "offered_load_vs_%d_slots" % args.slots: rate * mean_work / cap_slots,
+                   "rate_rule": ("0.8 x the measured single-stream capacity (%d jobs of the same mix, one at a "
+                                 "time, in work per second) / the mean work of the %d jobs" % (n_probe, n_jobs))
+                   if args.rate <= 0 else "given",
+                   "inputs": "simulated on the device before the run; copied to the host just ahead of arrival"},
         "serving": {"p50_latency_s": st["p50_s"], "p99_latency_s": st["p99_s"], "mean_latency_s": st["mean_s"],
                     "jobs_per_s": st["jobs_per_s"], "failed_jobs": st["failed"],
                     "cancelled_jobs": st["cancelled"], "max_device_bytes_admitted": int(srv.max_used),
-                    "budget_bytes": int(srv.mem_budget)},
+                    "budget_bytes": int(srv.mem_budget), "latency_breakdown": breakdown},
+        "gpu_launches": int(n_launch), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def aligned_error(J, Jt):
+    """max over stations of |J_p U - Jt_p|_F / |Jt_p|_F after the unitary U
+    that best maps J onto Jt (orthogonal Procrustes by SVD): the solution's
+    error with the gauge the unpolarised sky leaves free removed."""
+    M = np.einsum("pji,pjk->ik", J.conj(), Jt)
+    u, _, vh = np.linalg.svd(M)
+    U = u @ vh
+    return float(np.max(np.linalg.norm(J @ U - Jt, axis=(1, 2)) / np.linalg.norm(Jt, axis=(1, 2))))
+
+
+def run_consensus(args, rank, world, local_rank):
+    """Consensus across sub-bands: the bands' J-steps run at once on internal
+    streams (a workspace of several band workspaces) or one after another."""
+    import torch
+    from paper_1910_13908_gb300 import sagecal as sc
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    _, n_em, n_lm, desc = WORKLOADS["consensus16"]
+    prec = sc.SC_FP64 if args.prec == "fp64" else sc.SC_MIXED
+    n_bands, n_poly, n_admm, rho = 16, 3, 3, 1.0e4
+    spec = synth.JobSpec(N=128, T=10, F=2, K=10, S=25, seed=job_seed(rank))
+    fr, centres = synth.sub_bands(spec, n_bands)
+    basis = synth.frequency_basis(centres, n_poly)
+    Jt = synth.jones_true_bands(spec, centres)                       # [n_bands][K][N][2][2]
+    shp = sc.Shape(spec.N, spec.T, spec.F, spec.K, spec.S)
+    uvw = torch.as_tensor(synth.station_uvw(spec)).to(dev)
+    sky = synth.sky(spec)
+    dsky = sc.DeviceSky.from_synth(sky, dev)
+    cdt = torch.complex64 if prec == sc.SC_MIXED else torch.complex128
+    rdt = torch.float32 if prec == sc.SC_MIXED else torch.float64
+    ws1 = sc.workspace(shp, prec, dev)
+    p, q = np.triu_indices(spec.N, 1)
+    V = torch.zeros((n_bands, spec.T, spec.B, spec.F, 2, 2), dtype=cdt, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(4321 + spec.seed)
+    for f in range(n_bands):                       # inputs: the library's prediction, true Jones, noise
+        C = sc.predict_coherencies(shp, uvw, torch.as_tensor(fr[f]).to(dev), dsky, prec, ws1)
+        Jf = torch.as_tensor(Jt[f]).to(dev)
+        for k in range(spec.K):
+            G = (Jf[k, p] @ Jf[k, q].conj().transpose(-1, -2)).to(cdt)
+            V[f] += C[k][..., None, None] * G[None, :, None]
+        V[f] += torch.view_as_complex(torch.randn((*V[f].shape, 2), generator=g, device=dev, dtype=rdt) * spec.sigma)
+        del C
+    del ws1
+    dfr = torch.as_tensor(fr).to(dev)
+    dbasis = torch.as_tensor(basis).to(dev)
+    J0 = torch.as_tensor(np.broadcast_to(np.eye(2, dtype=complex), Jt.shape).copy()).to(dev)
+    conc = n_bands
+    ws = sc.consensus_workspace(shp, prec, conc, dev)
+
+    def run(w, r):
+        J = J0.clone()
+        sc.calibrate_consensus(shp, uvw, dfr, dsky, V, dbasis, J, prec, w, r, n_admm=n_admm, n_em=n_em, n_lm=n_lm,
+                               refine_sweeps=args.refine)
+        return J
+
+    def timed(w, r, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(k):
+            J = run(w, r)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k, J
+
+    for _ in range(args.warmup):
+        run(ws, rho)
+    clocks = ClockSampler(local_rank)
+    n0 = sc.launch_count()
+    ms, J = timed(ws, rho, args.steps)
+    n_launch = (sc.launch_count() - n0) // max(args.steps, 1)
+    clk = clocks.stop()
+    ms_seq, _ = timed(ws[: (sc.workspace_size(shp, prec) + 255) // 256 * 256], rho, 1)
+    _, J_ind = timed(ws, 0.0, 1)                  # rho = 0: each band alone
+    Jh, Jih = J.cpu().numpy(), J_ind.cpu().numpy()
+    err = np.array([[aligned_error(Jh[f, k], Jt[f, k]) for k in range(spec.K)] for f in range(n_bands)])
+    err_ind = np.array([[aligned_error(Jih[f, k], Jt[f, k]) for k in range(spec.K)] for f in range(n_bands)])
+    units = n_bands * spec.B * spec.T * spec.F * spec.K * n_lm * n_em * n_admm
+    line = {
+        "metric": METRIC, "value": units * world / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == sc.SC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": "consensus16", "description": desc, "bands": n_bands, "stations": spec.N,
+                   "baselines": spec.B, "timeslots": spec.T, "channels_per_band": spec.F, "clusters": spec.K,
+                   "sources_per_cluster": spec.S, "n_poly": n_poly, "rho": rho, "n_admm": n_admm,
+                   "concurrent_bands": conc, "l2": "inputs larger than L2 (%.2f GB of visibilities)"
+                   % (V.numel() * V.element_size() / 1e9)},
+        "consensus": {"ms_per_call_concurrent": ms, "ms_per_call_sequential": ms_seq,
+                      "speedup_concurrent": ms_seq / ms,
+                      "jones_error_consensus": {"median": float(np.median(err)), "max": float(err.max())},
+                      "jones_error_independent": {"median": float(np.median(err_ind)), "max": float(err_ind.max())},
+                      "error_measure": "max over stations of |J_p U - J_true,p| / |J_true,p| after Procrustes U, "
+                                       "per band and cluster"},
         "gpu_launches": int(n_launch), "clocks": clk,
     }
     if rank == 0:
@@ -992,6 +1143,8 @@ def main():
         elif args.workload == "serve500":
             args.jobs = args.jobs or 500
             run_serve(args, rank, world, local_rank)
+        elif args.workload == "consensus16":
+            run_consensus(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:
