@@ -62,7 +62,8 @@ WORKLOADS = {
                                "all chunks in one sc_calibrate_chunks call"),
     "batch64": ("c3", 3, 10, "64 sub-band jobs of 256 stations (32640 baselines), timeslots uniform in 5-40 "
                              "per job, 1 channel, 20 clusters x 50 sources, 3 SAGE sweeps x 10 LM, all jobs "
-                             "in one sc_calibrate_batch call"),
+                             "in one sc_calibrate_batched call (lock step: one launch per LM stage for all "
+                             "jobs)"),
 }
 
 
@@ -598,7 +599,10 @@ def measure_graph(job, spec, prec, J, costs, n_em, n_lm, args, units, flush, wor
 
 
 def run_batch(args, rank, world, local_rank):
-    """One step = one sc_calibrate_batch call over 64 uneven jobs."""
+    """One step = one sc_calibrate_batched call over 64 uneven jobs (lock
+    step: one launch per LM stage for every job).  The same jobs enqueued
+    job by job on their own streams (sc_calibrate_batch) are timed beside
+    it."""
     import torch
     from paper_1910_13908_gb300 import sagecal as sc
     dev = torch.device("cuda", local_rank)
@@ -617,15 +621,29 @@ def run_batch(args, rank, world, local_rank):
                            ws=job["ws"], stream=torch.cuda.Stream(dev)))
         J0s.append(job["J0"])
         units += spec.B * spec.T * spec.F * spec.K * n_lm * n_em
+    bws = sc.batched_workspace(jobs, prec, dev)
+    # the factorisation's task order, measured (untimed): staggered windows
+    # against the interleave (a window above the whole merged list)
+    window, tune_ms = sc.tune_batched(jobs, prec, bws, windows=(4, 16, 64, 1 << 20))
+    if window == 1 << 20:
+        window = 0                   # the interleave itself, without an order table
     torch.cuda.synchronize()
 
-    def step():
+    def step(lockstep=True):
         for j, j0 in zip(jobs, J0s):
             j.jones.copy_(j0)
         torch.cuda.synchronize()
-        sc.calibrate_batch(jobs, prec, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
+        if lockstep:
+            sc.calibrate_batched(jobs, prec, bws, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine, window=window)
+        else:
+            sc.calibrate_batch(jobs, prec, n_em=n_em, n_lm=n_lm, refine_sweeps=args.refine)
         torch.cuda.synchronize()
 
+    # the per-job-stream variant, for comparison (untimed warm-up, then one step)
+    step(False)
+    t0 = time.perf_counter()
+    step(False)
+    el_streams = time.perf_counter() - t0
     for _ in range(args.warmup):
         step()
     if world > 1:
@@ -650,8 +668,15 @@ def run_batch(args, rank, world, local_rank):
         "config": {"workload": "batch64", "description": desc, "jobs": n_jobs,
                    "timeslots_per_job": [int(t) for t in Ts], "precision": args.prec,
                    "timing": "host wall clock around each batch call with device synchronisation on both "
-                             "sides (the jobs run on 64 streams)",
+                             "sides",
+                   "batch_workspace_gb": bws.numel() / 1e9,
+                   "stagger_window": window,
+                   "tuner_ms_per_factorisation": {str(k): round(v, 3) for k, v in tune_ms.items()},
                    "l2": "inputs larger than L2"},
+        "streams_variant": {"entry": "sc_calibrate_batch (each job on its own stream, "
+                                     "CUDA_DEVICE_MAX_CONNECTIONS=%s)" % os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
+                            "value": units * world / max_over_ranks(el_streams, world, dev),
+                            "ms_per_step": 1e3 * el_streams},
         "gpu_launches": int(n_launch), "clocks": clk, "peak_kind": src,
     }
     if rank == 0:

@@ -537,9 +537,68 @@ typedef struct sc_job {
  * is capped (opts->lm.max_ctas, or an even share of the GPU when 0).  Results
  * of a job do not depend on the other jobs.  Returns when every job has been
  * enqueued; the first error (if any) is returned and later jobs are still
- * attempted. */
+ * attempted.  The device takes the streams' launches through a fixed number
+ * of hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless set before
+ * the process creates its CUDA context, at most 32); streams that share a
+ * queue wait on each other's launches, so overlap needs it raised (the
+ * Python package sets 32 at import unless the variable is set). */
 SC_API int32_t sc_calibrate_batch(const sc_job* jobs, int32_t n_jobs,
                                   const sc_sage_opts* opts, int32_t prec);
+
+/* Workspace of sc_calibrate_batched for these jobs (dims[n_jobs]; every job
+ * the N and K of job 0): one block per job holding the buffers of its
+ * cluster solves (Jones and LM state, statistics, the 8N x 8N matrix and
+ * its factor), about 4 (8 N)^2 bytes per job in SC_MIXED, and the task
+ * order of the batched factorisation (4 bytes per factorisation task of
+ * every job).  SC_EINVAL if the dimensions are invalid or differ in N or K. */
+SC_API int32_t sc_batched_workspace_size(const sc_dims* dims, int32_t n_jobs, int32_t prec, size_t* bytes);
+
+/* Many calibrations of equal station count N and cluster count K in lock
+ * step (paper §1: sub-bands and time chunks calibrated side by side; the
+ * jobs may differ in T, F, S_max, sky and data).  Each job is calibrated
+ * exactly as by sc_calibrate_sage with its own workspace (jobs[g].ws: its
+ * coherencies and running residual): the result of every job is bit for bit
+ * the one sc_calibrate_sage gives it.  Per cluster, each job's statistics
+ * pass runs over its own data; then every stage of the LM loop (Alg. 3.16
+ * of Madsen, Nielsen & Tingleff: assembly, factorisation, solves,
+ * refinement, trial, evaluation, decision) is one launch over all jobs.
+ * The factorisations of all jobs are one persistent kernel taking the
+ * tasks of the jobs' tile lists merged into one list in which each job
+ * keeps its own order.  window 0 interleaves the lists (task t of job g at
+ * position t * n_jobs + g: every job advances together, and the blocks
+ * waiting on one job's dependency chain are few among those working on the
+ * others).  window W in [1, 2^20] staggers the jobs instead: job g starts
+ * its list when job g - W is about to finish, so that about W matrices are
+ * read at a time; sc_tune_batched measures the choices.  ws:
+ * sc_batched_workspace_size bytes, 256-byte aligned, device memory owned by
+ * the caller.  Everything runs on `stream`, after what is already queued on
+ * each job's stream, and each job's stream then waits for the batch
+ * (events).  opts->lm.max_ctas caps the factorisation's blocks (0: all
+ * resident ones); opts->lm.chol_kernel must be SC_CHOL_SIMT.  Errors as
+ * sc_calibrate_sage (SC_EINVAL also for a window outside [0, 2^20]); a job's device status
+ * word gathers its solves'. */
+SC_API int32_t sc_calibrate_batched(const sc_job* jobs, int32_t n_jobs, const sc_sage_opts* opts, int32_t prec,
+                                    int32_t window, void* ws, size_t ws_bytes, void* stream);
+
+/* Autotuner of the batched factorisation: for each of windows[n_windows]
+ * (each in [1, 2^20]; one above (n_jobs - 1) x the tasks of one job
+ * orders the tasks as the interleave does), times `reps` factorisations of the
+ * jobs' matrix order (identity matrices: the arithmetic takes the same time
+ * on any values) in the batch workspace ws (sc_batched_workspace_size of
+ * dims), after one untimed run, with CUDA events on `stream`; writes the
+ * mean milliseconds per factorisation to ms_out[n_windows] and the fastest
+ * window to *best.  Synchronises `stream` (the one call of this library
+ * that does); overwrites ws.  SC_EINVAL for bad arguments or a batch too
+ * large for a staggered order. */
+SC_API int32_t sc_tune_batched(const sc_dims* dims, int32_t n_jobs, int32_t prec, const int32_t* windows,
+                               int32_t n_windows, int32_t reps, double* ms_out, int32_t* best, void* ws,
+                               size_t ws_bytes, void* stream);
+
+/* Host only, for tests: position in the merged factorisation task list of
+ * task t of job g, out[g * n + t], n the tasks per job of nT tile rows, for
+ * n_jobs jobs staggered over `window` jobs (as sc_calibrate_batched orders
+ * them).  cap: entries of out (>= n_jobs * n). */
+SC_API int32_t sc_batch_order(int32_t nT, int32_t n_jobs, int32_t window, int32_t* out, int64_t cap);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>
+#include <cstddef>
 #include <string>
 #include <thread>
 #include <vector>
@@ -490,6 +491,205 @@ static int consensus_streams(int m, cudaStream_t* st, cudaEvent_t* fork, cudaEve
   }
   for (int k = 0; k < m; ++k) st[k] = p.s[k], joins[k] = p.join[k];
   *fork = p.fork;
+  return SC_OK;
+}
+
+// ---- lock-step batch -------------------------------------------------------------------------
+
+// One job's block of a lock-step batch workspace: the buffers of a cluster
+// solve (the fields of a job workspace that the LM loop uses, the cluster's
+// w, statistics room for T_max timeslots).  Blocks follow each other at the
+// stride L.total, so that one launch moves every pointer by job * stride.
+static Workspace plan_lm_block(const Shape& s, int T_max) {
+  Workspace L{};
+  const size_t rs = s.prec == SC_MIXED ? 4 : 8;
+  const size_t N = s.N, B = (size_t)s.B;
+  L.Ppad = (int)((8 * N + kNB - 1) / kNB * kNB);
+  L.nT = L.Ppad / kNB;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  L.status = take(256);
+  L.lm = take(sizeof(LMState));
+  L.w = take(B * rs);
+  L.lstat = take(lm_stats_doubles(T_max, s.B) * 8);
+  L.part = take(lm_part_doubles(s.N) * 8);
+  L.J_old = take(8 * N * 8);
+  L.J_cur = take(8 * N * 8);
+  L.J_trial = take(8 * N * 8);
+  L.g_cur = take(8 * N * 8);
+  L.g_trial = take(8 * N * 8);
+  L.H_cur = take(4 * N * 8);
+  L.H_trial = take(4 * N * 8);
+  L.cpart_cur = take(N * 8);
+  L.cpart_trial = take(N * 8);
+  L.gm_cur = take(N * 8);
+  L.gm_trial = take(N * 8);
+  L.pred_part = take((8 * N / 256 + 1) * 8);
+  L.Jf_cur = take(8 * N * 4);
+  L.Jf_trial = take(8 * N * 4);
+  L.x = take((size_t)L.Ppad * 8);
+  L.rvec = take((size_t)L.Ppad * 8);
+  L.ry = take((size_t)L.Ppad * 8);
+  L.bvec = take((size_t)L.Ppad * 2 * rs);
+  L.A = take((size_t)L.Ppad * L.Ppad * rs);
+  L.Linv = take((size_t)L.nT * kNB * kNB * rs);
+  L.sync = take((size_t)chol_sync_ints(L.nT) * 4);
+  L.total = o;
+  return L;
+}
+
+// A lock-step batch workspace: G job blocks, then the combined task order
+// of the factorisation (G x tasks per job, uint32) when one can be formed.
+struct BatchedLayout {
+  Workspace block;
+  size_t order;  // offset of the order table; 0 if none
+  size_t total;
+};
+static BatchedLayout plan_batched(const Shape& s0, int T_max, int G) {
+  BatchedLayout b;
+  b.block = plan_lm_block(s0, T_max);
+  b.total = b.block.total * (size_t)G;
+  b.order = 0;
+  if (batch_order_ok(b.block.nT, G)) {
+    b.order = b.total;
+    b.total += align256((size_t)chol_ntasks(b.block.nT) * G * sizeof(uint32_t));
+  }
+  return b;
+}
+
+// SAGE on every job of a lock-step batch (equal N and K), all on c.st.
+// c: the batch workspace (c.L a block layout, c.s the shape of job 0);
+// jc: the jobs' own workspaces (coherencies, w, running residual).  Per
+// cluster, each job's statistics pass runs on its own data; then each LM
+// stage is one launch over all jobs, the factorisations one persistent
+// kernel; then each job's Jones and residual are updated.  Every job's
+// arithmetic is that of sage() alone.
+template <typename R>
+static int sage_batched(const Ctx& c, const std::vector<Ctx>& jc, const sc_job* jobs, const sc_sage_opts& o,
+                        const uint32_t* order) {
+  const int G = (int)jc.size();
+  const Shape& s = c.s;
+  const Workspace& L = c.L;
+  const size_t js = L.total;
+  const Batch bt{G, js};
+  const bool mixed = s.prec == SC_MIXED;
+  const size_t n8 = (size_t)8 * s.N * sizeof(double);
+  // job 0's buffers; the launches reach the others through the stride
+  LMBufs b{};
+  b.J_cur = c.at<double>(L.J_cur);
+  b.J_trial = c.at<double>(L.J_trial);
+  b.g_cur = c.at<double>(L.g_cur);
+  b.g_trial = c.at<double>(L.g_trial);
+  b.H_cur = c.at<double>(L.H_cur);
+  b.H_trial = c.at<double>(L.H_trial);
+  b.cp_cur = c.at<double>(L.cpart_cur);
+  b.cp_trial = c.at<double>(L.cpart_trial);
+  b.gm_cur = c.at<double>(L.gm_cur);
+  b.gm_trial = c.at<double>(L.gm_trial);
+  b.pred_part = c.at<double>(L.pred_part);
+  b.Jf_cur = mixed ? c.at<float>(L.Jf_cur) : nullptr;
+  b.Jf_trial = mixed ? c.at<float>(L.Jf_trial) : nullptr;
+  const R* Jr = nullptr;
+  if constexpr (sizeof(R) == 4) Jr = b.Jf_cur;
+  else Jr = b.J_cur;
+  double* x = c.at<double>(L.x);
+  double* rvec = c.at<double>(L.rvec);
+  double* stat = c.at<double>(L.lstat);
+  double* part = c.at<double>(L.part);
+  R* w = c.at<R>(L.w);
+  R* A = c.at<R>(L.A);
+  R* Linv = c.at<R>(L.Linv);
+  uint64_t* bw = c.at<uint64_t>(L.bvec);
+  int* sync = c.at<int>(L.sync);
+  LMState* lm = c.lm();
+  const int* nchunk_dev = &lm->nchunk;
+  auto blk = [&](int g) { return c.base + (size_t)g * js; };
+
+  // every job: coherencies and w, running residual R = V - sum_k model_k
+  SC_CUDA(cudaMemset2DAsync(c.base + L.status, js, 0, 256, G, c.st));
+  for (int g = 0; g < G; ++g) {
+    const Ctx& j = jc[g];
+    const size_t perC = (size_t)j.s.T * j.s.B * j.s.F * 2, perV = (size_t)j.s.T * j.s.B * j.s.F * 8;
+    R* C = j.at<R>(j.L.C);
+    R* Rres = j.at<R>(j.L.Rres);
+    int r = predict_all<R>(j, jobs[g].uvw, jobs[g].freqs, &jobs[g].sky, C, j.at<R>(j.L.w));
+    if (r) return r;
+    SC_CUDA(cudaMemcpyAsync(Rres, jobs[g].V, perV * sizeof(R), cudaMemcpyDeviceToDevice, c.st));
+    for (int k = 0; k < s.K; ++k)
+      SC_LAUNCH(PK_PASS, launch_pass<R>(j.s, P_SUB | P_WRITE_R, Rres, C + perC * k, nullptr,
+                                        jobs[g].jones + (size_t)8 * s.N * k, Rres, nullptr, nullptr, j.L.nchunk,
+                                        j.L.tchunk, nullptr, c.st));
+  }
+  for (int em = 0; em < o.n_em; ++em) {
+    for (int k = 0; k < s.K; ++k) {
+      // per job: the cluster's Jones, w and statistics into its block
+      for (int g = 0; g < G; ++g) {
+        const Ctx& j = jc[g];
+        const size_t perC = (size_t)j.s.T * j.s.B * j.s.F * 2;
+        char* bg = blk(g);
+        double* Jk = jobs[g].jones + (size_t)8 * s.N * k;
+        double* J_old = reinterpret_cast<double*>(bg + L.J_old);
+        SC_CUDA(cudaMemcpyAsync(J_old, Jk, n8, cudaMemcpyDeviceToDevice, c.st));
+        SC_CUDA(cudaMemcpyAsync(bg + L.J_cur, Jk, n8, cudaMemcpyDeviceToDevice, c.st));
+        SC_CUDA(cudaMemcpyAsync(bg + L.w, j.at<R>(j.L.w) + (size_t)s.B * k, (size_t)s.B * sizeof(R),
+                                cudaMemcpyDeviceToDevice, c.st));
+        int nst = 0;
+        SC_LAUNCH(PK_STATS, launch_lm_stats<R>(j.s, j.at<R>(j.L.Rres), j.at<R>(j.L.C) + perC * k, J_old,
+                                               reinterpret_cast<double*>(bg + L.lstat), &nst, c.st,
+                                               reinterpret_cast<int*>(bg + L.lm + offsetof(LMState, nchunk))));
+      }
+      SC_CUDA(cudaMemset2DAsync(x, js, 0, (size_t)L.Ppad * sizeof(double), G, c.st));
+      SC_CUDA(cudaMemset2DAsync(rvec, js, 0, (size_t)L.Ppad * sizeof(double), G, c.st));
+      SC_CUDA(cudaMemset2DAsync(bw, js, 0, (size_t)L.Ppad * 2 * sizeof(R), G, c.st));  // no stale tag can match
+      // the LM loop, one launch per stage for every job
+      SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, 0, b.J_cur, part, nullptr, c.st, bt, nchunk_dev));
+      SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, b.J_cur, b.g_cur, b.H_cur, b.cp_cur, b.gm_cur, nullptr,
+                                              nullptr, 0.0, c.st, bt));
+      SC_LAUNCH(PK_LM, launch_lm_init(lm, &o.lm, s.N, b, b.J_cur, c.st, bt));
+      for (int it = 0; it < o.lm.n_lm; ++it) {
+        SC_LAUNCH(PK_ASSEMBLE, launch_assemble<R>(s, L.Ppad, L.Ppad, w, Jr, b.H_cur, lm, A, true, false, c.st, bt));
+        SC_LAUNCH(PK_CHOL, launch_chol_batch<R>(A, L.Ppad, L.nT, Linv, sync, c.status(), lm, o.lm.max_ctas, bt,
+                                                order, c.st));
+        SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, b.g_cur, bw, x, 0, c.status(), lm,
+                                                 c.st, bt));
+        if (mixed) {
+          for (int sw = 0; sw < o.lm.refine_sweeps; ++sw) {
+            SC_LAUNCH(PK_REFINE, launch_refine_residual<R>(s, w, b.J_cur, b.H_cur, b.g_cur, x, lm,
+                                                           c.at<double>(L.ry), rvec, c.st, bt));
+            SC_LAUNCH(PK_SOLVE, launch_chol_solve<R>(A, L.Ppad, L.nT, Linv, sync, rvec, bw, x, 1, c.status(), lm,
+                                                     c.st, bt));
+          }
+        }
+        SC_LAUNCH(PK_LM, launch_lm_trial(lm, s.N, x, b, c.st, bt));
+        SC_LAUNCH(PK_REDUCE, launch_lm_eval<R>(s, true, stat, 0, b.J_trial, part, lm, c.st, bt, nchunk_dev));
+        SC_LAUNCH(PK_REDUCE, launch_station_sum(s, part, b.J_trial, b.g_trial, b.H_trial, b.cp_trial, b.gm_trial,
+                                                lm, nullptr, 0.0, c.st, bt));
+        SC_LAUNCH(PK_LM, launch_lm_decide(lm, s.N, b, c.st, bt));
+      }
+      // per job: the new Jones and the residual R += c (J_old J_old^H - J_new J_new^H)
+      for (int g = 0; g < G; ++g) {
+        const Ctx& j = jc[g];
+        const size_t perC = (size_t)j.s.T * j.s.B * j.s.F * 2;
+        char* bg = blk(g);
+        double* Jk = jobs[g].jones + (size_t)8 * s.N * k;
+        SC_LAUNCH(PK_LM, launch_lm_finish(reinterpret_cast<LMState*>(bg + L.lm),
+                                          reinterpret_cast<double*>(bg + L.J_cur), s.N, Jk,
+                                          jobs[g].costs ? jobs[g].costs + k : nullptr, nullptr, c.st));
+        R* Rres = j.at<R>(j.L.Rres);
+        SC_LAUNCH(PK_PASS, launch_pass<R>(j.s, P_OLD | P_SUB | P_WRITE_R, Rres, j.at<R>(j.L.C) + perC * k,
+                                          reinterpret_cast<double*>(bg + L.J_old), Jk, Rres, nullptr, nullptr,
+                                          j.L.nchunk, j.L.tchunk, nullptr, c.st));
+      }
+    }
+  }
+  // each job's status word gathers its block's
+  for (int g = 0; g < G; ++g)
+    SC_LAUNCH(PK_OTHER, launch_or_status(reinterpret_cast<const uint32_t*>(blk(g) + L.status), jc[g].status(),
+                                         c.st));
   return SC_OK;
 }
 
@@ -1004,6 +1204,188 @@ SC_API int32_t sc_calibrate_batch(const sc_job* jobs, int32_t n_jobs, const sc_s
       if (!m.empty()) return fail(r, "%s", m.c_str());
     return fail(r, "a job failed");
   }
+  return ok();
+}
+
+// checks of a lock-step batch that touch no device memory; T_max of the jobs
+static int check_batched(const sc_dims* dims, int32_t n_jobs, int32_t prec, Shape& s0, int& T_max) {
+  if (n_jobs < 1 || dims == nullptr) return fail(SC_EINVAL, "a batch needs at least one job");
+  T_max = 0;
+  for (int g = 0; g < n_jobs; ++g) {
+    Shape s;
+    if (check_dims(&dims[g], prec, s)) {
+      const std::string m = g_msg;
+      return fail(SC_EINVAL, "job %d: %s", g, m.c_str());
+    }
+    if (g == 0) s0 = s;
+    else if (s.N != s0.N || s.K != s0.K)
+      return fail(SC_EINVAL, "job %d has N = %d, K = %d; a lock-step batch needs the N and K of job 0 (%d, %d)", g,
+                  s.N, s.K, s0.N, s0.K);
+    T_max = std::max(T_max, s.T);
+  }
+  return SC_OK;
+}
+
+SC_API int32_t sc_batched_workspace_size(const sc_dims* dims, int32_t n_jobs, int32_t prec, size_t* bytes) {
+  Shape s0;
+  int T_max = 0;
+  int r = check_batched(dims, n_jobs, prec, s0, T_max);
+  if (r) return r;
+  if (!bytes) return fail(SC_EINVAL, "bytes is NULL");
+  *bytes = plan_batched(s0, T_max, n_jobs).total;
+  return ok();
+}
+
+SC_API int32_t sc_calibrate_batched(const sc_job* jobs, int32_t n_jobs, const sc_sage_opts* opts, int32_t prec,
+                                    int32_t window, void* ws, size_t ws_bytes, void* stream) {
+  if (n_jobs < 1 || jobs == nullptr) return fail(SC_EINVAL, "a batch needs at least one job");
+  if (!opts) return fail(SC_EINVAL, "options are NULL");
+  if (opts->n_em < 0) return fail(SC_EINVAL, "n_em must be >= 0");
+  int r = check_lm(&opts->lm);
+  if (r) return r;
+  if (opts->lm.chol_kernel != SC_CHOL_SIMT)
+    return fail(SC_EINVAL, "the batched factorisation has only the SC_CHOL_SIMT kernel");
+  if (window < 0 || window > (1 << 20)) return fail(SC_EINVAL, "window must be in [0, 2^20]");
+  std::vector<sc_dims> dims(n_jobs);
+  for (int g = 0; g < n_jobs; ++g) dims[g] = jobs[g].dims;
+  Shape s0;
+  int T_max = 0;
+  if ((r = check_batched(dims.data(), n_jobs, prec, s0, T_max))) return r;
+  for (int g = 0; g < n_jobs; ++g) {
+    const sc_job& j = jobs[g];
+    Shape sj;
+    check_dims(&j.dims, prec, sj);
+    if (check_sky(sj, &j.sky)) {
+      const std::string m = g_msg;
+      return fail(SC_EINVAL, "job %d: %s", g, m.c_str());
+    }
+    if (!j.uvw || !j.freqs || !j.V || !j.jones)
+      return fail(SC_EINVAL, "job %d: uvw, freqs, V and jones must not be NULL", g);
+    if (!j.ws || (reinterpret_cast<uintptr_t>(j.ws) & 255))
+      return fail(SC_EINVAL, "job %d: workspace NULL or not 256-byte aligned", g);
+    const size_t need = plan_workspace(sj, true).total;
+    if (j.ws_bytes < need) return fail(SC_ENOMEM, "job %d: workspace of %zu bytes, %zu needed", g, j.ws_bytes, need);
+  }
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(SC_EINVAL, "batch workspace NULL or not 256-byte aligned");
+  Ctx c;
+  c.s = s0;
+  const BatchedLayout bl = plan_batched(s0, T_max, n_jobs);
+  c.L = bl.block;
+  if (ws_bytes < bl.total) return fail(SC_ENOMEM, "batch workspace of %zu bytes, %zu needed", ws_bytes, bl.total);
+  c.base = static_cast<char*>(ws);
+  c.st = static_cast<cudaStream_t>(stream);
+  c.splits = 1;
+  // the batch runs on `stream` after the work already queued on each job's stream
+  for (int g = 0; g < n_jobs; ++g) {
+    if (jobs[g].stream == stream) continue;
+    cudaEvent_t ev = nullptr;
+    SC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    SC_CUDA(cudaEventRecord(ev, static_cast<cudaStream_t>(jobs[g].stream)));
+    SC_CUDA(cudaStreamWaitEvent(c.st, ev, 0));
+    SC_CUDA(cudaEventDestroy(ev));
+  }
+  std::vector<Ctx> jc(n_jobs);
+  for (int g = 0; g < n_jobs; ++g)
+    if ((r = open_ctx(jc[g], &jobs[g].dims, prec, jobs[g].ws, jobs[g].ws_bytes, stream))) return r;
+  uint32_t* order = nullptr;  // window 0: the lists interleaved, no table
+  if (window > 0) {
+    if (!bl.order) return fail(SC_EINVAL, "these jobs are too many or too large for a staggered order");
+    order = c.at<uint32_t>(bl.order);
+    SC_LAUNCH(PK_OTHER, launch_batch_order(c.L.nT, n_jobs, window, order, c.st));
+  }
+  r = prec == SC_MIXED ? sage_batched<float>(c, jc, jobs, *opts, order)
+                       : sage_batched<double>(c, jc, jobs, *opts, order);
+  if (r) return r;
+  // each job's stream continues after the batch
+  cudaEvent_t done = nullptr;
+  SC_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+  SC_CUDA(cudaEventRecord(done, c.st));
+  for (int g = 0; g < n_jobs; ++g)
+    if (jobs[g].stream != stream) SC_CUDA(cudaStreamWaitEvent(static_cast<cudaStream_t>(jobs[g].stream), done, 0));
+  SC_CUDA(cudaEventDestroy(done));
+  return ok();
+}
+
+SC_API int32_t sc_tune_batched(const sc_dims* dims, int32_t n_jobs, int32_t prec, const int32_t* windows,
+                                int32_t n_windows, int32_t reps, double* ms_out, int32_t* best, void* ws,
+                                size_t ws_bytes, void* stream) {
+  Shape s0;
+  int T_max = 0;
+  int r = check_batched(dims, n_jobs, prec, s0, T_max);
+  if (r) return r;
+  if (n_windows < 1 || windows == nullptr || ms_out == nullptr || best == nullptr || reps < 1)
+    return fail(SC_EINVAL, "windows, ms_out and best must not be NULL, n_windows and reps >= 1");
+  for (int i = 0; i < n_windows; ++i)
+    if (windows[i] < 1 || windows[i] > (1 << 20))
+      return fail(SC_EINVAL, "window %d is %d; windows must be in [1, 2^20]", i, windows[i]);
+  if (ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(SC_EINVAL, "batch workspace NULL or not 256-byte aligned");
+  const BatchedLayout bl = plan_batched(s0, T_max, n_jobs);
+  if (ws_bytes < bl.total) return fail(SC_ENOMEM, "batch workspace of %zu bytes, %zu needed", ws_bytes, bl.total);
+  if (!bl.order) return fail(SC_EINVAL, "these jobs are too many or too large for a staggered order");
+  Ctx c;
+  c.s = s0;
+  c.L = bl.block;
+  c.base = static_cast<char*>(ws);
+  c.st = static_cast<cudaStream_t>(stream);
+  c.splits = 1;
+  const Workspace& L = c.L;
+  const size_t js = L.total;
+  const Batch bt{n_jobs, js};
+  const size_t rs = prec == SC_MIXED ? 4 : 8;
+  // identity matrices (the arithmetic takes the same time on any values),
+  // LM states that are not done, clear status words
+  SC_CUDA(cudaMemset2DAsync(c.base + L.A, js, 0, (size_t)L.Ppad * L.Ppad * rs, n_jobs, c.st));
+  SC_CUDA(cudaMemset2DAsync(c.base + L.lm, js, 0, sizeof(LMState), n_jobs, c.st));
+  SC_CUDA(cudaMemset2DAsync(c.base + L.status, js, 0, 256, n_jobs, c.st));
+  for (int g = 0; g < n_jobs; ++g) {
+    char* A = c.base + (size_t)g * js + L.A;
+    if (prec == SC_MIXED) SC_CUDA(launch_pad_identity(reinterpret_cast<float*>(A), L.Ppad, 0, c.st));
+    else SC_CUDA(launch_pad_identity(reinterpret_cast<double*>(A), L.Ppad, 0, c.st));
+  }
+  uint32_t* order = c.at<uint32_t>(bl.order);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SC_CUDA(cudaEventCreate(&e0));
+  SC_CUDA(cudaEventCreate(&e1));
+  auto factor = [&]() -> cudaError_t {
+    return prec == SC_MIXED
+               ? launch_chol_batch<float>(c.at<float>(L.A), L.Ppad, L.nT, c.at<float>(L.Linv), c.at<int>(L.sync),
+                                          c.status(), c.lm(), 0, bt, order, c.st)
+               : launch_chol_batch<double>(c.at<double>(L.A), L.Ppad, L.nT, c.at<double>(L.Linv),
+                                           c.at<int>(L.sync), c.status(), c.lm(), 0, bt, order, c.st);
+  };
+  int bi = 0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n_windows && e == cudaSuccess; ++i) {
+    const int W = windows[i];
+    // each run factorises identities again: the factor of I is I
+    if ((e = launch_batch_order(L.nT, n_jobs, W, order, c.st)) != cudaSuccess) break;
+    if ((e = factor()) != cudaSuccess) break;  // warm-up
+    if ((e = cudaEventRecord(e0, c.st)) != cudaSuccess) break;
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = factor();
+    if (e != cudaSuccess || (e = cudaEventRecord(e1, c.st)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+    ms_out[i] = ms / reps;
+    if (ms_out[i] < ms_out[bi]) bi = i;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "tuning the batched factorisation: %s", cudaGetErrorString(e));
+  *best = windows[bi];
+  return ok();
+}
+
+SC_API int32_t sc_batch_order(int32_t nT, int32_t n_jobs, int32_t window, int32_t* out, int64_t cap) {
+  if (nT < 1 || n_jobs < 1 || window < 1 || window > (1 << 20) || !batch_order_ok(nT, n_jobs) || out == nullptr)
+    return fail(SC_EINVAL, "bad batch order arguments");
+  const int n = chol_ntasks(nT);
+  if (cap < (int64_t)n * n_jobs) return fail(SC_EINVAL, "out holds %lld entries, %lld needed", (long long)cap,
+                                              (long long)n * n_jobs);
+  for (int g = 0; g < n_jobs; ++g)
+    for (int t = 0; t < n; ++t) out[(size_t)g * n + t] = batch_order_pos(n, n_jobs, window, g, t);
   return ok();
 }
 

@@ -867,6 +867,195 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
 }
 
 
+// Position m of the combined task list of a batch: (job, task of that job's
+// list).  With an order table (k_batch_order), entry m holds job << 20 |
+// task; without one, the lists are interleaved.  An entry outside the
+// batch gives job -1 (no task: a table that is not a permutation leaves
+// tasks undone, which the bounded waits report, instead of stray pointers).
+__device__ __forceinline__ void batch_task(const uint32_t* __restrict__ order, int m, int G, int n, int& job,
+                                           int& t) {
+  if (order != nullptr) {
+    const uint32_t e = __ldg(order + m);
+    job = (int)(e >> 20);
+    t = (int)(e & 0xFFFFFu);
+    if (job >= G || t >= n) job = -1;
+  } else {
+    job = m % G;
+    t = m / G;
+  }
+}
+
+// The factorisations of a lock-step batch of G jobs in one persistent
+// launch, taking the tasks of a combined list in which every job's tasks
+// keep their own order (the order table staggers the jobs; see
+// batch_order_pos).  The dependencies of a task (earlier tasks of its own
+// job) therefore lie earlier in the combined list, and the list-order
+// argument against deadlock carries over.
+// There is no walker: the diagonal chain's tasks come from the list like
+// the others, a POTRF running alone in its block (nothing queued behind
+// it), and while one job's chain is waited on, the other blocks find the
+// other jobs' tiles.  Each tile is formed by the same arithmetic as in
+// k_chol (its walker's POTRF, TRSM and diagonal UPDATE included), so every
+// job's factor is bit for bit the one k_chol gives.  The counter is job 0's;
+// tiles, counters, status and LM state are the task's job's.
+template <typename R>
+__global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_batch(R* __restrict__ A0, int lda, int nT,
+                                                            R* __restrict__ Linv0, int n_tasks, int G, size_t js,
+                                                            const uint32_t* __restrict__ order,
+                                                            int* sync0, uint32_t* status0, LMState* lm0) {
+  constexpr int LD = Pitch<R>::value;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* s0 = reinterpret_cast<R*>(smraw);
+  R* s1 = s0 + kNB * LD;
+  R* s2 = s1 + kNB * LD;
+  R* aux = s2 + kNB * LD;  // POTRF scratch; the second Y buffer otherwise
+  auto Xb = [&](int b) { return b ? s2 : s0; };
+  auto Yb = [&](int b) { return b ? aux : s1; };
+  __shared__ int s_task, s_ok, s_bad;
+  int* const counter = SyncView(sync0, nT).fctr;
+  const int total = n_tasks * G;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int next = -1;  // thread 0: the claimed, not yet examined task
+  int4 cur = make_int4(-1, 0, 0, 0);
+  int cjob = 0;       // cur's job
+  bool have = false;  // cur's operands are queued in buffer pair buf
+  int buf = 0;
+  for (;;) {
+    if (!have) {
+      __syncthreads();  // every thread has read the previous s_task and left shared memory
+      if (threadIdx.x == 0) {
+        s_task = next >= 0 ? next : atomicAdd(counter, 1);
+        next = -1;
+      }
+      __syncthreads();
+      const int m = s_task;
+      if (m >= total) break;
+      int job, t;
+      batch_task(order, m, G, n_tasks, job, t);
+      if (job < 0) continue;
+      LMState* lm = job_ptr(lm0, js, job);
+      if (lm != nullptr && lm->done) continue;
+      R* A = job_ptr(A0, js, job);
+      R* Linv = job_ptr(Linv0, js, job);
+      const SyncView sv(job_ptr(sync0, js, job), nT);
+      uint32_t* status = job_ptr(status0, js, job);
+      cur = chol_task(nT, t);
+      cjob = job;
+      if (cur.x == T_POTRF) {
+        const int j = cur.w;
+        if (threadIdx.x == 0) {
+          s_ok = wait_ge(sv.upd + j * nT + j, j, status);
+          s_bad = 0;
+        }
+        __syncthreads();
+        if (!s_ok) {
+          if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
+          break;
+        }
+        R* Ajj = A + (size_t)j * kNB * lda + (size_t)j * kNB;
+        load_tile(s0, Ajj, lda);
+        __syncthreads();
+        potrf_tile(s0, s1, aux, &s_bad);  // s0 = L_jj, s1 = Linv_jj
+        store_tile(Ajj, lda, s0);
+        store_tile(Linv + (size_t)j * kNB * kNB, kNB, s1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          if (s_bad) {
+            atomicOr(status, SC_STATUS_NOTPD);
+            if (lm != nullptr) lm->notpd = 1;
+          }
+          st_release(sv.pdone + j, 1);
+        }
+        continue;
+      }
+      if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+      bool ok = true;
+      if (threadIdx.x < 3) {
+        const int* p;
+        int v;
+        task_dep(cur, nT, sv, threadIdx.x, p, v);
+        if (p != nullptr) ok = wait_ge(p, v, status);
+      }
+      if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
+        break;
+      }
+      task_operands_async(cur, A, lda, Linv, Xb(buf), Yb(buf));
+      have = true;
+    }
+    // look at the claimed next task; queue its operands if it is a ready
+    // TRSM or UPDATE (a POTRF waits for the buffers to be free)
+    if (threadIdx.x == 0) s_task = next;
+    __syncthreads();
+    const int t2 = s_task;
+    int4 nxt = make_int4(-1, 0, 0, 0);
+    int njob = 0;
+    bool staged = false;
+    if (t2 >= 0 && t2 < total) {
+      int nt;
+      batch_task(order, t2, G, n_tasks, njob, nt);
+      const LMState* nlm = njob < 0 ? nullptr : job_ptr(lm0, js, njob);
+      if (njob < 0 || (nlm != nullptr && nlm->done)) {
+        if (threadIdx.x == 0) next = -1;  // a finished job: nothing to do
+      } else {
+        nxt = chol_task(nT, nt);
+        if (nxt.x != T_POTRF) {
+          const SyncView nsv(job_ptr(sync0, js, njob), nT);
+          bool ready = true;
+          if (threadIdx.x < 3) {
+            const int* p;
+            int v;
+            task_dep(nxt, nT, nsv, threadIdx.x, p, v);
+            if (p != nullptr) ready = ld_acquire(p) >= v;
+          }
+          staged = __syncthreads_and(ready) != 0;
+          if (staged) {
+            if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+            task_operands_async(nxt, job_ptr(A0, js, njob), lda, job_ptr(Linv0, js, njob), Xb(buf ^ 1),
+                                Yb(buf ^ 1));
+          }
+        }
+      }
+    }
+    // the current task
+    R* A = job_ptr(A0, js, cjob);
+    const SyncView sv(job_ptr(sync0, js, cjob), nT);
+    const int i = cur.y, k = cur.z, j = cur.w;
+    const bool trsm = cur.x == T_TRSM;
+    R* Out = A + (size_t)i * kNB * lda + (size_t)(trsm ? j : k) * kNB;
+    R old[4][4];  // an UPDATE's output tile, fetched while the operands arrive
+    if (!trsm) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) old[a][b] = __ldcg(Out + (size_t)(ty + 16 * a) * lda + tx + 16 * b);
+    }
+    if (staged) async_wait_prev();
+    else async_wait_all();
+    __syncthreads();
+    R acc[4][4];
+    gemm_nt(acc, Xb(buf), Yb(buf));
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        __stcg(Out + (size_t)(ty + 16 * a) * lda + tx + 16 * b, trsm ? acc[a][b] : old[a][b] - acc[a][b]);
+    __syncthreads();  // the tile is stored and buffer pair buf is free
+    if (threadIdx.x == 32) {
+      if (trsm) st_release(sv.tdone + i * nT + j, 1);
+      else st_release(sv.upd + i * nT + k, j + 1);
+    }
+    if (staged) {
+      cur = nxt;
+      cjob = njob;
+      buf ^= 1;
+    } else {
+      have = false;
+    }
+  }
+  async_wait_all();
+}
+
 // The factorisation kernel of the float32 path: the walker as in k_chol; the
 // bulk TRSM/UPDATE tasks on the tensor cores, two deep.  Shared memory holds
 // two stages of raw operands (X, Y: 32 KB each) and one region for the low
@@ -1208,6 +1397,81 @@ template cudaError_t launch_chol<float>(float*, int, int, float*, int*, uint32_t
 template cudaError_t launch_chol<double>(double*, int, int, double*, int*, uint32_t*, LMState*, int, int,
                                          cudaStream_t);
 
+// Blocks of k_chol_batch: as many as are resident at once, computed once.
+template <typename R>
+static int chol_batch_grid(size_t smem) {
+  static const int cached = [&] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void* fn = reinterpret_cast<const void*>(&k_chol_batch<R>);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCholThreads, smem);
+    return std::max(1, sms * std::min(std::max(per, 1), 4));
+  }();
+  return cached;
+}
+
+template <typename R>
+cudaError_t launch_chol_batch(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
+                              int max_ctas, const Batch& bt, const uint32_t* order, cudaStream_t st) {
+  const int n_tasks = chol_ntasks(nT);
+  if (bt.G < 1 || (long long)n_tasks * bt.G > (1LL << 30)) return cudaErrorInvalidValue;
+  if (order != nullptr && (bt.G > 4096 || n_tasks > (1 << 20))) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(R) * (4 * kNB) * Pitch<R>::value;
+  int grid = std::min<long long>(chol_batch_grid<R>(smem), (long long)n_tasks * bt.G);
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
+  // every job's counters: rows of the reset length at the job stride
+  const size_t row = sizeof(int) * chol_factor_reset_ints(nT);
+  cudaError_t e = bt.G == 1 ? cudaMemsetAsync(sync, 0, row, st) : cudaMemset2DAsync(sync, bt.js, 0, row, bt.G, st);
+  if (e != cudaSuccess) return e;
+  k_chol_batch<R><<<grid, kCholThreads, smem, st>>>(A, lda, nT, Linv, n_tasks, bt.G, bt.js, order, sync, status,
+                                                     lm);
+  return cudaGetLastError();
+}
+template cudaError_t launch_chol_batch<float>(float*, int, int, float*, int*, uint32_t*, LMState*, int,
+                                              const Batch&, const uint32_t*, cudaStream_t);
+template cudaError_t launch_chol_batch<double>(double*, int, int, double*, int*, uint32_t*, LMState*, int,
+                                               const Batch&, const uint32_t*, cudaStream_t);
+
+// The combined task list of a batch's factorisations, the jobs staggered
+// over a window of W jobs.  Job g's task t (of n per job) gets the key
+// (t + 1) W + g n, i.e. its progress through its own list plus g / W of a
+// list, and the combined list is sorted by (key, job): job g starts when
+// job g - W is about to finish, so about W jobs are in flight at once, in
+// different phases (one job's chain-bound last panels beside another's
+// work-rich first ones), and only their matrices are being read.  Within a
+// job the key grows with t, so every job keeps its own order.  The position
+// of (g, t) counts, for every job g', the tasks with a smaller key (ties:
+// the lower job first), in O(G).
+__host__ __device__ int batch_order_pos(int n, int G, int W, int g, int t) {
+  long long pos = 0;
+  for (int h = 0; h < G; ++h) {
+    // tasks t' of job h with (t' + 1) W < D, and one with (t' + 1) W == D
+    const long long D = (long long)(t + 1) * W + (long long)(g - h) * n;
+    if (D > W) pos += std::min<long long>(n, (D - 1) / W);
+    if (h < g && D % W == 0 && D / W >= 1 && D / W <= n) pos += 1;
+  }
+  return (int)pos;
+}
+
+__global__ void k_batch_order(int n, int G, int W, uint32_t* __restrict__ order) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)n * G) return;
+  const int g = (int)(i / n), t = (int)(i % n);
+  const int p = batch_order_pos(n, G, W, g, t);
+  if (p >= 0 && (long long)p < (long long)n * G) order[p] = ((uint32_t)g << 20) | (uint32_t)t;
+}
+
+bool batch_order_ok(int nT, int G) { return G >= 1 && G <= 4096 && chol_ntasks(nT) <= (1 << 20); }
+
+cudaError_t launch_batch_order(int nT, int G, int W, uint32_t* order, cudaStream_t st) {
+  if (!batch_order_ok(nT, G) || W < 1 || W > (1 << 20)) return cudaErrorInvalidValue;
+  const long long total = (long long)chol_ntasks(nT) * G;
+  k_batch_order<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(chol_ntasks(nT), G, W, order);
+  return cudaGetLastError();
+}
+
 // ---- triangular solves ------------------------------------------------------------------------
 
 // Asynchronous copy of one 64x64 tile into shared memory as one commit group.
@@ -1370,15 +1634,19 @@ __device__ bool get_tagged(const uint64_t* w, uint32_t tag, R& v, uint32_t* stat
 // buffers while the task waits for their blocks.  y_i and then x_i occupy
 // the tagged words of row i (BWD(i) runs after every FWD task has finished,
 // so no reader of y_i remains when x_i replaces it).
+//
+// A lock-step batch of G jobs takes the tasks of one combined list: task t
+// is task t / G of job t mod G (dependencies stay earlier in the list); the
+// counter is job 0's, every other pointer is the task's job's.
 template <typename R>
-__global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict__ A, int lda, int nT,
-                                                            const R* __restrict__ Linv,
-                                                            int n_tasks, int* sync,
-                                                            const double* __restrict__ b,
-                                                            uint64_t* __restrict__ yw, double* __restrict__ x,
+__global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict__ A0, int lda, int nT,
+                                                            const R* __restrict__ Linv0,
+                                                            int n_tasks, int* sync0,
+                                                            const double* __restrict__ b0,
+                                                            uint64_t* __restrict__ yw0, double* __restrict__ x0,
                                                             int accumulate, uint32_t tag_fwd,
-                                                            uint32_t* status, const LMState* lm) {
-  if (lm != nullptr && (lm->done | lm->notpd)) return;
+                                                            uint32_t* status0, const LMState* lm0, int G,
+                                                            size_t js) {
   constexpr int LD = Pitch<R>::value;
   constexpr int NW = sizeof(R) / 4;  // tagged words per value
   const uint32_t tag_bwd = tag_fwd + 1;
@@ -1389,7 +1657,14 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
   R* B1 = B0 + kNB * LD;
   R* vin = B1 + kNB * LD;
   __shared__ int s_task, s_ok;
-  SyncView sv(sync, nT);
+  int* const counter = SyncView(sync0, nT).sctr;
+  // the current task's job
+  const R* A = A0;
+  const R* Linv = Linv0;
+  const double* b = b0;
+  uint64_t* yw = yw0;
+  double* x = x0;
+  uint32_t* status = status0;
   const int tid = threadIdx.x;
   // forward: quad r = tid / 4 owns entry r (acc[0]); backward: lane group
   // g = tid / 16 owns entries 4g..4g+3
@@ -1411,12 +1686,21 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_solve(const R* __restrict
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      s_task = atomicAdd(sv.sctr, 1);
+      s_task = atomicAdd(counter, 1);
       s_ok = 1;  // before the barrier: later failure reports cannot be lost
     }
     __syncthreads();
-    const int t = s_task;
-    if (t >= n_tasks) break;
+    const int tg = s_task;
+    if (tg >= n_tasks * G) break;
+    const int job = tg % G, t = tg / G;
+    const LMState* lm = job_ptr(lm0, js, job);
+    if (lm != nullptr && (lm->done | lm->notpd)) continue;
+    A = job_ptr(A0, js, job);
+    Linv = job_ptr(Linv0, js, job);
+    b = job_ptr(b0, js, job);
+    yw = job_ptr(yw0, js, job);
+    x = job_ptr(x0, js, job);
+    status = job_ptr(status0, js, job);
     const int4 tk = solve_task(nT, t);
     const int i = tk.y;
     const bool fwd = tk.x == T_FWD;
@@ -1510,8 +1794,9 @@ static std::atomic<uint32_t> g_solve_launches{0};
 template <typename R>
 cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* sync,
                               const double* b, uint64_t* bwork, double* x, int accumulate,
-                              uint32_t* status, const LMState* lm, cudaStream_t st) {
+                              uint32_t* status, const LMState* lm, cudaStream_t st, const Batch& bt) {
   int n_tasks = 2 * nT;
+  if ((long long)n_tasks * bt.G > (1LL << 30)) return cudaErrorInvalidValue;
   size_t smem = sizeof(R) * (4 * kNB * Pitch<R>::value + kNB);
   static const bool attr_set = [&] {
     cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_chol_solve<R>),
@@ -1524,15 +1809,15 @@ cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* s
   SyncView sv(sync, nT);
   cudaError_t err = cudaMemsetAsync(sv.sctr, 0, sizeof(int), st);
   if (err != cudaSuccess) return err;
-  k_chol_solve<R><<<n_tasks, kCholThreads, smem, st>>>(A, lda, nT, Linv, n_tasks, sync, b, bwork, x, accumulate,
-                                                       2 * e, status, lm);
+  k_chol_solve<R><<<n_tasks * bt.G, kCholThreads, smem, st>>>(A, lda, nT, Linv, n_tasks, sync, b, bwork, x,
+                                                              accumulate, 2 * e, status, lm, bt.G, bt.js);
   return cudaGetLastError();
 }
 template cudaError_t launch_chol_solve<float>(const float*, int, int, const float*, int*,
                                               const double*, uint64_t*, double*, int, uint32_t*,
-                                              const LMState*, cudaStream_t);
+                                              const LMState*, cudaStream_t, const Batch&);
 template cudaError_t launch_chol_solve<double>(const double*, int, int, const double*, int*,
                                                const double*, uint64_t*, double*, int, uint32_t*,
-                                               const LMState*, cudaStream_t);
+                                               const LMState*, cudaStream_t, const Batch&);
 
 }  // namespace sc

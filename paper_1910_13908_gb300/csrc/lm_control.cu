@@ -51,7 +51,11 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-__global__ void k_lm_init(LMState* lm, sc_lm_opts o, int N, LMBufs b, const double* __restrict__ J_src) {
+__global__ void k_lm_init(LMState* lm, sc_lm_opts o, int N, LMBufs b, const double* __restrict__ J_src, size_t js) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
+  b = job_bufs(b, js, job);
+  J_src = job_ptr(J_src, js, job);
   __shared__ double sh[32];
   __shared__ unsigned long long shu[32];
   double c = 0.0;
@@ -88,16 +92,20 @@ __global__ void k_lm_init(LMState* lm, sc_lm_opts o, int N, LMBufs b, const doub
 }
 
 cudaError_t launch_lm_init(LMState* lm, const sc_lm_opts* o, int N, const LMBufs& b, const double* J_src,
-                           cudaStream_t st) {
-  k_lm_init<<<1, 512, 0, st>>>(lm, *o, N, b, J_src);
+                           cudaStream_t st, const Batch& bt) {
+  k_lm_init<<<dim3(1, 1, bt.G), 512, 0, st>>>(lm, *o, N, b, J_src, bt.js);
   return cudaGetLastError();
 }
 
 // One thread per parameter: theta_trial = theta + d, and per block the
 // partial predicted decrease sum d (mu d + g).
 __global__ void __launch_bounds__(kTrialThreads) k_lm_trial(LMState* lm, int N, const double* __restrict__ x,
-                                                          LMBufs b) {
+                                                          LMBufs b, size_t js) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
   if (lm->done) return;
+  b = job_bufs(b, js, job);
+  x = job_ptr(x, js, job);
   __shared__ double sh[32];
   if (lm->notpd) {
     if (blockIdx.x == 0 && threadIdx.x == 0) lm->skip = 1;
@@ -122,13 +130,17 @@ __global__ void __launch_bounds__(kTrialThreads) k_lm_trial(LMState* lm, int N, 
 
 int lm_trial_blocks(int N) { return (8 * N + kTrialThreads - 1) / kTrialThreads; }
 
-cudaError_t launch_lm_trial(LMState* lm, int N, const double* x, const LMBufs& b, cudaStream_t st) {
-  k_lm_trial<<<lm_trial_blocks(N), kTrialThreads, 0, st>>>(lm, N, x, b);
+cudaError_t launch_lm_trial(LMState* lm, int N, const double* x, const LMBufs& b, cudaStream_t st,
+                            const Batch& bt) {
+  k_lm_trial<<<dim3(lm_trial_blocks(N), 1, bt.G), kTrialThreads, 0, st>>>(lm, N, x, b, bt.js);
   return cudaGetLastError();
 }
 
-__global__ void k_lm_decide(LMState* lm, int N, int n_pred, LMBufs b) {
+__global__ void k_lm_decide(LMState* lm, int N, int n_pred, LMBufs b, size_t js) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
   if (lm->done) return;
+  b = job_bufs(b, js, job);
   __shared__ double sh[32];
   __shared__ unsigned long long shu[32];
   __shared__ int s_accept;
@@ -182,8 +194,8 @@ __global__ void k_lm_decide(LMState* lm, int N, int n_pred, LMBufs b) {
   }
 }
 
-cudaError_t launch_lm_decide(LMState* lm, int N, const LMBufs& b, cudaStream_t st) {
-  k_lm_decide<<<1, 512, 0, st>>>(lm, N, lm_trial_blocks(N), b);
+cudaError_t launch_lm_decide(LMState* lm, int N, const LMBufs& b, cudaStream_t st, const Batch& bt) {
+  k_lm_decide<<<dim3(1, 1, bt.G), 512, 0, st>>>(lm, N, lm_trial_blocks(N), b, bt.js);
   return cudaGetLastError();
 }
 

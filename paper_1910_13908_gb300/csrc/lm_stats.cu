@@ -138,7 +138,9 @@ template <int FL>
 __global__ void __launch_bounds__(kStatThreads) k_lm_stats64(int N, int T, int F, int64_t B, int nchunk, int tchunk,
                                                            const double* __restrict__ Xin,
                                                            const double* __restrict__ C,
-                                                           const double* __restrict__ J_old, double* __restrict__ stat) {
+                                                           const double* __restrict__ J_old, double* __restrict__ stat,
+                                                           int* __restrict__ nchunk_out) {
+  if (nchunk_out != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *nchunk_out = nchunk;
   const int64_t n_items = (int64_t)nchunk * B;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_items;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -210,7 +212,9 @@ template <int FL>
 __global__ void __launch_bounds__(kStatThreads) k_lm_stats32(int N, int T, int F, int64_t B, int nchunk, int tchunk,
                                                            const float* __restrict__ Xin,
                                                            const float* __restrict__ C,
-                                                           const double* __restrict__ J_old, double* __restrict__ stat) {
+                                                           const double* __restrict__ J_old, double* __restrict__ stat,
+                                                           int* __restrict__ nchunk_out) {
+  if (nchunk_out != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *nchunk_out = nchunk;
   extern __shared__ __align__(16) unsigned char st_smem[];
   float4* xring = reinterpret_cast<float4*>(st_smem);                                        // [kRing][2][T]
   float2* cring = reinterpret_cast<float2*>(st_smem + (size_t)kRing * 2 * kStatThreads * 16);  // [kRing][T]
@@ -314,7 +318,7 @@ struct StatsKernel<double> {
 
 template <typename R, int FL>
 static cudaError_t go_stats(const Shape& s, const R* Xin, const R* C, const double* J_old, double* stat,
-                            int* nchunk, cudaStream_t st) {
+                            int* nchunk, int* nchunk_dev, cudaStream_t st) {
   using K = StatsKernel<R>;
   // resident blocks of this instantiation, computed once (thread-safe static)
   static const int resident = [] {
@@ -332,22 +336,23 @@ static cudaError_t go_stats(const Shape& s, const R* Xin, const R* C, const doub
   const int64_t items = (int64_t)nc * s.B;
   const unsigned grid = (unsigned)std::min<int64_t>((items + kStatThreads - 1) / kStatThreads, resident);
   if constexpr (sizeof(R) == 4)
-    k_lm_stats32<FL><<<grid, kStatThreads, K::smem, st>>>(s.N, s.T, s.F, s.B, nc, tc, Xin, C, J_old, stat);
+    k_lm_stats32<FL><<<grid, kStatThreads, K::smem, st>>>(s.N, s.T, s.F, s.B, nc, tc, Xin, C, J_old, stat,
+                                                          nchunk_dev);
   else
-    k_lm_stats64<FL><<<grid, kStatThreads, 0, st>>>(s.N, s.T, s.F, s.B, nc, tc, Xin, C, J_old, stat);
+    k_lm_stats64<FL><<<grid, kStatThreads, 0, st>>>(s.N, s.T, s.F, s.B, nc, tc, Xin, C, J_old, stat, nchunk_dev);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_lm_stats(const Shape& s, const R* Xin, const R* C, const double* J_old, double* stat,
-                            int* nchunk, cudaStream_t st) {
-  return J_old != nullptr ? go_stats<R, P_OLD>(s, Xin, C, J_old, stat, nchunk, st)
-                          : go_stats<R, 0>(s, Xin, C, J_old, stat, nchunk, st);
+                            int* nchunk, cudaStream_t st, int* nchunk_dev) {
+  return J_old != nullptr ? go_stats<R, P_OLD>(s, Xin, C, J_old, stat, nchunk, nchunk_dev, st)
+                          : go_stats<R, 0>(s, Xin, C, J_old, stat, nchunk, nchunk_dev, st);
 }
 template cudaError_t launch_lm_stats<float>(const Shape&, const float*, const float*, const double*, double*, int*,
-                                            cudaStream_t);
+                                            cudaStream_t, int*);
 template cudaError_t launch_lm_stats<double>(const Shape&, const double*, const double*, const double*, double*,
-                                             int*, cudaStream_t);
+                                             int*, cudaStream_t, int*);
 
 // ---- one LM evaluation: per-station sums from the statistics ------------------------------
 //
@@ -459,8 +464,15 @@ template <typename R, bool SUB>
 __global__ void __launch_bounds__(kST * kST) k_lm_eval(int N, int64_t B, int nS, int nchunk,
                                                      const double* __restrict__ stat,
                                                      const double* __restrict__ J, double* __restrict__ part,
-                                                     const LMState* __restrict__ lm) {
+                                                     const LMState* __restrict__ lm, size_t js,
+                                                     const int* __restrict__ nchunk_dev) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
   if (lm != nullptr && (lm->done | lm->skip)) return;
+  stat = job_ptr(stat, js, job);
+  J = job_ptr(J, js, job);
+  part = job_ptr(part, js, job);
+  if (nchunk_dev != nullptr) nchunk = *job_ptr(nchunk_dev, js, job);
   __shared__ R colbuf[kColV][kST][kST + 1];
   const int pair = blockIdx.x;
   // tile pairs (Pt, Qt), Pt <= Qt, are numbered like the baselines of nS + 1
@@ -527,16 +539,17 @@ __global__ void __launch_bounds__(kST * kST) k_lm_eval(int N, int64_t B, int nS,
 
 template <typename R>
 cudaError_t launch_lm_eval(const Shape& s, bool sub, const double* stat, int nchunk, const double* J, double* part,
-                           const LMState* lm, cudaStream_t st) {
+                           const LMState* lm, cudaStream_t st, const Batch& bt, const int* nchunk_dev) {
   const int nS = (s.N + kST - 1) / kST, pairs = nS * (nS + 1) / 2;
-  if (sub) k_lm_eval<R, true><<<pairs, kST * kST, 0, st>>>(s.N, s.B, nS, nchunk, stat, J, part, lm);
-  else k_lm_eval<R, false><<<pairs, kST * kST, 0, st>>>(s.N, s.B, nS, nchunk, stat, J, part, lm);
+  const dim3 grd(pairs, 1, bt.G);
+  if (sub) k_lm_eval<R, true><<<grd, kST * kST, 0, st>>>(s.N, s.B, nS, nchunk, stat, J, part, lm, bt.js, nchunk_dev);
+  else k_lm_eval<R, false><<<grd, kST * kST, 0, st>>>(s.N, s.B, nS, nchunk, stat, J, part, lm, bt.js, nchunk_dev);
   return cudaGetLastError();
 }
 template cudaError_t launch_lm_eval<float>(const Shape&, bool, const double*, int, const double*, double*,
-                                           const LMState*, cudaStream_t);
+                                           const LMState*, cudaStream_t, const Batch&, const int*);
 template cudaError_t launch_lm_eval<double>(const Shape&, bool, const double*, int, const double*, double*,
-                                            const LMState*, cudaStream_t);
+                                            const LMState*, cudaStream_t, const Batch&, const int*);
 
 // One warp per station s.  Lane (h, v), h = lane / 16 and v = lane % 16 < 13,
 // adds value v of every other partial of the list
@@ -553,8 +566,18 @@ __global__ void __launch_bounds__(kSumThreads) k_station_sum(int N, int nS, cons
                                                              double* __restrict__ H, double* __restrict__ cpart,
                                                              double* __restrict__ gmax,
                                                              const LMState* __restrict__ lm,
-                                                             const double* __restrict__ pen, double pen_w) {
+                                                             const double* __restrict__ pen, double pen_w,
+                                                             size_t js) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
   if (lm != nullptr && (lm->done | lm->skip)) return;
+  part = job_ptr(part, js, job);
+  J = job_ptr(J, js, job);
+  g = job_ptr(g, js, job);
+  H = job_ptr(H, js, job);
+  cpart = job_ptr(cpart, js, job);
+  gmax = job_ptr(gmax, js, job);
+  pen = job_ptr(pen, js, job);
   const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (s >= N) return;  // whole warps leave together
   const int St = s / kST, sl = s % kST;
@@ -607,10 +630,11 @@ __global__ void __launch_bounds__(kSumThreads) k_station_sum(int N, int nS, cons
 
 cudaError_t launch_station_sum(const Shape& s, const double* part, const double* J, double* g, double* H,
                                double* cpart, double* gmax, const LMState* lm, const double* pen, double pen_w,
-                               cudaStream_t st) {
+                               cudaStream_t st, const Batch& bt) {
   const int nS = (s.N + kST - 1) / kST;
   const unsigned blocks = (unsigned)((s.N + kSumThreads / 32 - 1) / (kSumThreads / 32));
-  k_station_sum<<<blocks, kSumThreads, 0, st>>>(s.N, nS, part, J, g, H, cpart, gmax, lm, pen, pen_w);
+  const dim3 grd(blocks, 1, bt.G);
+  k_station_sum<<<grd, kSumThreads, 0, st>>>(s.N, nS, part, J, g, H, cpart, gmax, lm, pen, pen_w, bt.js);
   return cudaGetLastError();
 }
 

@@ -41,8 +41,14 @@ __global__ void __launch_bounds__(256) k_assemble(int N, int lda, int Ppad, cons
                                                   const R* __restrict__ J,
                                                   const double* __restrict__ H,
                                                   const LMState* __restrict__ lm, R* __restrict__ A,
-                                                  int damp, int full) {
+                                                  int damp, int full, size_t js) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
   if (lm != nullptr && lm->done) return;
+  w = job_ptr(w, js, job);
+  J = job_ptr(J, js, job);
+  H = job_ptr(H, js, job);
+  A = job_ptr(A, js, job);
   int P = 8 * N;
   int row = blockIdx.y;
   int col0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -119,18 +125,18 @@ cudaError_t launch_round_jones(const double* J, float* Jf, int n, cudaStream_t s
 template <typename R>
 cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const R* J,
                             const double* H, const LMState* lm, R* A, bool damp, bool full,
-                            cudaStream_t st) {
+                            cudaStream_t st, const Batch& bt) {
   int groups = (Ppad + 3) / 4;
-  dim3 grd((groups + 127) / 128, Ppad);
-  k_assemble<R><<<grd, 128, 0, st>>>(s.N, lda, Ppad, w, J, H, lm, A, damp ? 1 : 0, full ? 1 : 0);
+  dim3 grd((groups + 127) / 128, Ppad, bt.G);
+  k_assemble<R><<<grd, 128, 0, st>>>(s.N, lda, Ppad, w, J, H, lm, A, damp ? 1 : 0, full ? 1 : 0, bt.js);
   return cudaGetLastError();
 }
 template cudaError_t launch_assemble<float>(const Shape&, int, int, const float*, const float*,
                                             const double*, const LMState*, float*, bool, bool,
-                                            cudaStream_t);
+                                            cudaStream_t, const Batch&);
 template cudaError_t launch_assemble<double>(const Shape&, int, int, const double*, const double*,
                                              const double*, const LMState*, double*, bool, bool,
-                                             cudaStream_t);
+                                             cudaStream_t, const Batch&);
 
 // Ones on the diagonal of rows n..Ppad-1 of a zeroed padded matrix, so that
 // the padding factorises as the identity.
@@ -164,8 +170,14 @@ __device__ __forceinline__ m22<double> ld_m22(const double* p) {
 // butterfly within each warp and a fixed-order sum over the warps.
 __global__ void __launch_bounds__(256) k_refine_prep(int N, const double* __restrict__ J,
                                                      const double* __restrict__ x,
-                                                     const LMState* __restrict__ lm, double* __restrict__ Y) {
+                                                     const LMState* __restrict__ lm, double* __restrict__ Y,
+                                                     size_t js) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
   if (lm->done | lm->notpd) return;
+  J = job_ptr(J, js, job);
+  x = job_ptr(x, js, job);
+  Y = job_ptr(Y, js, job);
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= N) return;
   const m22<double> t = h_mul(ld_m22(x + 8 * o), load_jones<double>(J, o));
@@ -183,8 +195,17 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_refine_residual(int N, co
                                                          const double* __restrict__ x,
                                                          const double* __restrict__ Y,
                                                          const LMState* __restrict__ lm,
-                                                         double* __restrict__ r) {
+                                                         double* __restrict__ r, size_t js) {
+  const int job = blockIdx.z;
+  lm = job_ptr(lm, js, job);
   if (lm->done | lm->notpd) return;
+  w = job_ptr(w, js, job);
+  J = job_ptr(J, js, job);
+  H = job_ptr(H, js, job);
+  g = job_ptr(g, js, job);
+  x = job_ptr(x, js, job);
+  Y = job_ptr(Y, js, job);
+  r = job_ptr(r, js, job);
   __shared__ double part[kRefineWarps][8];
   const int s = blockIdx.x, lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   double k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -229,18 +250,18 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_refine_residual(int N, co
 template <typename R>
 cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, const double* H,
                                    const double* g, const double* x, const LMState* lm,
-                                   double* Y, double* r, cudaStream_t st) {
-  k_refine_prep<<<(s.N + 255) / 256, 256, 0, st>>>(s.N, J, x, lm, Y);
+                                   double* Y, double* r, cudaStream_t st, const Batch& bt) {
+  k_refine_prep<<<dim3((s.N + 255) / 256, 1, bt.G), 256, 0, st>>>(s.N, J, x, lm, Y, bt.js);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_refine_residual<R><<<s.N, 32 * kRefineWarps, 0, st>>>(s.N, w, J, H, g, x, Y, lm, r);
+  k_refine_residual<R><<<dim3(s.N, 1, bt.G), 32 * kRefineWarps, 0, st>>>(s.N, w, J, H, g, x, Y, lm, r, bt.js);
   return cudaGetLastError();
 }
 template cudaError_t launch_refine_residual<float>(const Shape&, const float*, const double*,
                                                    const double*, const double*, const double*,
-                                                   const LMState*, double*, double*, cudaStream_t);
+                                                   const LMState*, double*, double*, cudaStream_t, const Batch&);
 template cudaError_t launch_refine_residual<double>(const Shape&, const double*, const double*,
                                                     const double*, const double*, const double*,
-                                                    const LMState*, double*, double*, cudaStream_t);
+                                                    const LMState*, double*, double*, cudaStream_t, const Batch&);
 
 }  // namespace sc

@@ -148,7 +148,8 @@ struct LMState {
   double cost, cost_trial, pred, rho;
   double lm_tau, eps_grad;
   int32_t iter, n_lm, done, notpd, skip, accepted;
-  int32_t pad[2];
+  int32_t nchunk;  // timeslot chunks of the statistics (set by the statistics pass of a batched solve)
+  int32_t pad;
 };
 
 // Device buffers of one LM solve's state: current and trial Jones,
@@ -160,6 +161,27 @@ struct LMBufs {
   double* pred_part;
   float *Jf_cur, *Jf_trial;
 };
+
+// A lock-step batch: G jobs of equal station count whose LM buffers lie at a
+// fixed byte stride js from those of job 0.  Each launch covers every job;
+// a kernel takes its job from blockIdx.z (the persistent factorisation and
+// the solves from the task index) and moves every buffer pointer by
+// job * js.  G = 1, js = 0 is a single solve.
+struct Batch {
+  int G = 1;
+  size_t js = 0;
+};
+template <typename T>
+__host__ __device__ __forceinline__ T* job_ptr(T* p, size_t js, int g) {
+  return p == nullptr ? p : reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + (size_t)g * js);
+}
+__host__ __device__ __forceinline__ LMBufs job_bufs(LMBufs b, size_t js, int g) {
+  return {job_ptr(b.J_cur, js, g),   job_ptr(b.J_trial, js, g),  job_ptr(b.g_cur, js, g),
+          job_ptr(b.g_trial, js, g), job_ptr(b.H_cur, js, g),    job_ptr(b.H_trial, js, g),
+          job_ptr(b.cp_cur, js, g),  job_ptr(b.cp_trial, js, g), job_ptr(b.gm_cur, js, g),
+          job_ptr(b.gm_trial, js, g), job_ptr(b.pred_part, js, g), job_ptr(b.Jf_cur, js, g),
+          job_ptr(b.Jf_trial, js, g)};
+}
 
 // ---- workspace ------------------------------------------------------------------------
 
@@ -298,15 +320,19 @@ cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, con
 // launch_station_sum adds them into g [8N], H [4N] and the station costs
 // cpart [N] (and the per-station maxima of |J^T r|, gmax [N]), plus the
 // penalty pen_w |theta - pen|^2 if pen is not NULL.
+// nchunk_dev, if not NULL, also receives the chunk count on the device.
+// In a batch, launch_lm_eval reads each job's chunk count from nchunk_dev
+// (moved by the job stride) when it is not NULL, else takes nchunk.
 template <typename R>
 cudaError_t launch_lm_stats(const Shape& s, const R* Xin, const R* C, const double* J_old, double* stat,
-                            int* nchunk, cudaStream_t st);
+                            int* nchunk, cudaStream_t st, int* nchunk_dev = nullptr);
 template <typename R>
 cudaError_t launch_lm_eval(const Shape& s, bool sub, const double* stat, int nchunk, const double* J, double* part,
-                           const LMState* lm, cudaStream_t st);
+                           const LMState* lm, cudaStream_t st, const Batch& bt = Batch{},
+                           const int* nchunk_dev = nullptr);
 cudaError_t launch_station_sum(const Shape& s, const double* part, const double* J, double* g, double* H,
                                double* cpart, double* gmax, const LMState* lm, const double* pen, double pen_w,
-                               cudaStream_t st);
+                               cudaStream_t st, const Batch& bt = Batch{});
 size_t lm_stats_doubles(int T, int64_t B);  // size of stat for any GPU of at most kMaxSMs SMs
 size_t lm_part_doubles(int N);              // size of the per-tile partials
 cudaError_t launch_sum_cost(const double* cpart, int N, double* out, cudaStream_t st);
@@ -329,13 +355,13 @@ cudaError_t launch_residual_all(const Shape& s, const R* V, const R* C, const R*
 template <typename R>
 cudaError_t launch_assemble(const Shape& s, int lda, int Ppad, const R* w, const R* J,
                             const double* H, const LMState* lm, R* A, bool damp, bool full,
-                            cudaStream_t st);
+                            cudaStream_t st, const Batch& bt = Batch{});
 cudaError_t launch_round_jones(const double* J, float* Jf, int n, cudaStream_t st);
 // r = g - (J^T J + mu I) x in float64; Y [8N] is scratch
 template <typename R>
 cudaError_t launch_refine_residual(const Shape& s, const R* w, const double* J, const double* H,
                                    const double* g, const double* x, const LMState* lm,
-                                   double* Y, double* r, cudaStream_t st);
+                                   double* Y, double* r, cudaStream_t st, const Batch& bt = Batch{});
 
 // normal_eqs.cu: identity on rows n..Ppad-1 of a zeroed padded matrix
 template <typename R>
@@ -350,17 +376,31 @@ int chol_sync_ints(int nT);
 template <typename R>
 cudaError_t launch_chol(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
                         int max_ctas, int kernel, cudaStream_t st);
+// The factorisations of a whole batch as one persistent launch: the task
+// lists of the G jobs interleaved (task t is task t / G of job t mod G), no
+// walker; every tile is computed by the same arithmetic as in launch_chol.
+template <typename R>
+cudaError_t launch_chol_batch(R* A, int lda, int nT, R* Linv, int* sync, uint32_t* status, LMState* lm,
+                              int max_ctas, const Batch& bt, const uint32_t* order, cudaStream_t st);
+// The combined task order of a batch with the jobs staggered over a window
+// of W jobs: entry m is job << 20 | task (order [G * chol_ntasks(nT)]).
+// Possible when batch_order_ok (G <= 4096, at most 2^20 tasks per job);
+// otherwise the factorisation interleaves the lists (order NULL).
+__host__ __device__ int batch_order_pos(int n, int G, int W, int g, int t);
+bool batch_order_ok(int nT, int G);
+cudaError_t launch_batch_order(int nT, int G, int W, uint32_t* order, cudaStream_t st);
 template <typename R>
 cudaError_t launch_chol_solve(const R* A, int lda, int nT, const R* Linv, int* sync,
                               const double* b, uint64_t* bwork, double* x, int accumulate,
-                              uint32_t* status, const LMState* lm, cudaStream_t st);
+                              uint32_t* status, const LMState* lm, cudaStream_t st, const Batch& bt = Batch{});
 
 // lm_control.cu
 cudaError_t launch_lm_init(LMState* lm, const sc_lm_opts* o, int N, const LMBufs& b, const double* J_src,
-                           cudaStream_t st);
-cudaError_t launch_lm_trial(LMState* lm, int N, const double* x, const LMBufs& b, cudaStream_t st);
+                           cudaStream_t st, const Batch& bt = Batch{});
+cudaError_t launch_lm_trial(LMState* lm, int N, const double* x, const LMBufs& b, cudaStream_t st,
+                            const Batch& bt = Batch{});
 int lm_trial_blocks(int N);
-cudaError_t launch_lm_decide(LMState* lm, int N, const LMBufs& b, cudaStream_t st);
+cudaError_t launch_lm_decide(LMState* lm, int N, const LMBufs& b, cudaStream_t st, const Batch& bt = Batch{});
 cudaError_t launch_lm_finish(const LMState* lm, const double* J_cur, int N, double* J_out,
                              double* cost_out, int32_t* iters_out, cudaStream_t st);
 

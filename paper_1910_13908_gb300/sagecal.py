@@ -115,6 +115,13 @@ def lib():
         for f in ("sc_graph_capture_sage", "sc_graph_launch", "sc_graph_destroy"):
             getattr(L, f).restype = i32
         L.sc_calibrate_batch.restype = i32
+        L.sc_batched_workspace_size.argtypes = [D, i32, i32, _c.POINTER(sz)]
+        L.sc_calibrate_batched.argtypes = [_c.POINTER(JobC), i32, _c.POINTER(SageOpts), i32, i32, vp, sz, vp]
+        L.sc_tune_batched.argtypes = [D, i32, i32, _c.POINTER(i32), i32, i32, _c.POINTER(_c.c_double),
+                                      _c.POINTER(i32), vp, sz, vp]
+        L.sc_batch_order.argtypes = [i32, i32, i32, _c.POINTER(i32), _c.c_int64]
+        for f in ("sc_batched_workspace_size", "sc_calibrate_batched", "sc_tune_batched", "sc_batch_order"):
+            getattr(L, f).restype = i32
         L.sc_cholesky_workspace_size.argtypes = [i32, i32, _c.POINTER(sz)]
         L.sc_cholesky_solve.argtypes = [i32, vp, i32, vp, vp, i32, i32, vp, sz, vp]
         for f in ("sc_cholesky_workspace_size", "sc_cholesky_solve"):
@@ -603,6 +610,15 @@ def calibrate_batch(jobs, prec: int, n_em=1, n_lm=10, refine_sweeps=1, tau=1e-3,
                     max_ctas=0):
     """Enqueue every job (sc_calibrate_batch); each runs on job.stream.
     Synchronise the streams (or the device) before reading the results."""
+    arr, keep = _job_array(jobs, prec)
+    o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas))
+    _check(lib().sc_calibrate_batch(arr, len(jobs), _c.byref(o), prec))
+    del keep
+    return jobs
+
+
+def _job_array(jobs, prec):
+    """The jobs as sc_job structs (and the sky structs they point to)."""
     n = len(jobs)
     arr = (JobC * n)()
     keep = []
@@ -615,9 +631,61 @@ def calibrate_batch(jobs, prec: int, n_em=1, n_lm=10, refine_sweeps=1, tau=1e-3,
         keep.append(skc)
         arr[i] = JobC(d.c(), _ptr(j.uvw), _ptr(j.freqs), skc, _ptr(j.V), _ptr(j.jones), _ptr(j.costs),
                       _ptr(j.ws), j.ws.numel(), _c.c_void_p(j.stream.cuda_stream))
+    return arr, keep
+
+
+def _job_dims(jobs):
+    dims = (Dims * len(jobs))()
+    for i, j in enumerate(jobs):
+        dims[i] = Shape(j.shape.N, j.shape.T, j.shape.F, j.sky.K, max(j.shape.S_max, j.sky.S_max)).c()
+    return dims
+
+
+def batched_workspace(jobs, prec: int, device="cuda"):
+    """Workspace of calibrate_batched for these jobs (sc_batched_workspace_size)."""
+    import torch
+    n = len(jobs)
+    dims = _job_dims(jobs)
+    nb = _c.c_size_t(0)
+    _check(lib().sc_batched_workspace_size(dims, n, prec, _c.byref(nb)))
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=device)
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+def calibrate_batched(jobs, prec: int, ws, n_em=1, n_lm=10, refine_sweeps=1, tau=1e-3, eps_grad=1e-12,
+                      max_ctas=0, window=0):
+    """Lock-step batch (sc_calibrate_batched) of jobs of equal N and K on the
+    current stream, the factorisations staggered over `window` jobs (0: as
+    many as fit in L2); each job's stream waits for it."""
+    arr, keep = _job_array(jobs, prec)
     o = SageOpts(int(n_em), lm_opts(n_lm, refine_sweeps, tau, eps_grad, max_ctas))
-    _check(lib().sc_calibrate_batch(arr, n, _c.byref(o), prec))
+    _check(lib().sc_calibrate_batched(arr, len(jobs), _c.byref(o), prec, int(window), _ptr(ws), ws.numel(),
+                                      _stream()))
+    del keep
     return jobs
+
+
+def tune_batched(jobs, prec: int, ws, windows=(1, 4, 16, 64, 1 << 20), reps=3):
+    """sc_tune_batched: ms per batched factorisation for each window; returns
+    (best window, {window: ms}).  Synchronises; overwrites ws."""
+    n = len(windows)
+    w = (_c.c_int32 * n)(*[int(x) for x in windows])
+    ms = (_c.c_double * n)()
+    best = _c.c_int32(0)
+    _check(lib().sc_tune_batched(_job_dims(jobs), len(jobs), prec, w, n, int(reps), ms, _c.byref(best),
+                                 _ptr(ws), ws.numel(), _stream()))
+    return best.value, {int(windows[i]): ms[i] for i in range(n)}
+
+
+def batch_order(nT: int, n_jobs: int, window: int):
+    """Host only: positions [n_jobs][tasks per job] of each job's tasks in the
+    merged factorisation list (sc_batch_order)."""
+    import numpy as np
+    n = _check(lib().sc_chol_schedule(nT, 0, None, 0))
+    out = (_c.c_int32 * (n * n_jobs))()
+    _check(lib().sc_batch_order(nT, n_jobs, window, out, n * n_jobs))
+    return np.frombuffer(out, dtype=np.int32).reshape(n_jobs, n).copy()
 
 
 def torch_complex128():

@@ -1,6 +1,8 @@
 """The C-ABI library loads on a machine without a GPU and exports every entry
 point that include/*.h declares; host-only calls work without a device."""
 import ctypes
+
+import numpy as np
 import glob
 import os
 import re
@@ -213,3 +215,64 @@ def test_consensus_rejects_bad_arguments_before_touching_the_device(lib):
     buf = ctypes.create_string_buffer(256)
     L.sc_last_error(buf, 256)
     assert b"must not be NULL" in buf.value
+
+
+def test_lockstep_batch_task_list_keeps_each_jobs_dependencies_earlier():
+    """The batched factorisation and solves take task t of a combined list as
+    task t // G of job t % G.  Every job's dependencies then come earlier in
+    the combined list, in the same relative order as in its own list, so the
+    list-order argument against deadlock holds for the batch as well."""
+    for nT, G in ((3, 2), (5, 3), (9, 5)):
+        own = sagecal.chol_schedule(nT, 0)
+        combined = [(t % G, own[t // G]) for t in range(len(own) * G)]
+        for g in range(G):
+            mine = [task for job, task in combined if job == g]
+            assert mine == own
+        # position of each job's task in the combined list grows with its own position
+        pos = {}
+        for t, (g, task) in enumerate(combined):
+            pos[(g, tuple(task))] = t
+        for g in range(G):
+            order = [pos[(g, tuple(task))] for task in own]
+            assert order == sorted(order)
+
+
+def test_batched_workspace_size_is_host_only(lib):
+    L = sagecal.lib()
+    dims = (sagecal.Dims * 3)(sagecal.Shape(70, 3, 2, 2, 5).c(), sagecal.Shape(70, 9, 1, 2, 4).c(),
+                               sagecal.Shape(70, 1, 4, 2, 6).c())
+    n3 = ctypes.c_size_t(0)
+    assert L.sc_batched_workspace_size(dims, 3, sagecal.SC_MIXED, ctypes.byref(n3)) == 0
+    one = (sagecal.Dims * 1)(sagecal.Shape(70, 9, 1, 2, 4).c())
+    n1 = ctypes.c_size_t(0)
+    assert L.sc_batched_workspace_size(one, 1, sagecal.SC_MIXED, ctypes.byref(n1)) == 0
+    # one block per job, each sized for the largest job's statistics, then
+    # the merged task order (4 bytes per factorisation task of every job)
+    tasks = len(sagecal.chol_schedule((8 * 70 + 63) // 64, 0))
+    a256 = lambda x: (x + 255) // 256 * 256
+    block = n1.value - a256(4 * tasks)
+    assert n3.value == 3 * block + a256(3 * 4 * tasks)
+    P = 8 * 70
+    assert n1.value > 4 * P * P                      # the float32 matrix of one job
+    bad = (sagecal.Dims * 2)(sagecal.Shape(70, 3, 2, 2, 5).c(), sagecal.Shape(71, 3, 2, 2, 5).c())
+    assert L.sc_batched_workspace_size(bad, 2, sagecal.SC_MIXED, ctypes.byref(n3)) == -1
+    assert L.sc_batched_workspace_size(bad, 0, sagecal.SC_MIXED, ctypes.byref(n3)) == -1
+
+
+def test_staggered_batch_order_is_a_permutation_keeping_each_jobs_order(lib):
+    """The staggered merge of the jobs' factorisation lists (positions from
+    the closed form the device kernel uses) fills every slot exactly once,
+    keeps each job's own order (so dependencies stay earlier: no deadlock),
+    and with window W has job g start after job g - W has done most of its
+    list."""
+    for nT, G, W in ((1, 1, 1), (3, 2, 1), (5, 3, 2), (9, 7, 3), (9, 7, 7), (17, 5, 64), (32, 64, 6)):
+        pos = sagecal.batch_order(nT, G, W)
+        n = pos.shape[1]
+        assert sorted(pos.ravel().tolist()) == list(range(n * G)), (nT, G, W)
+        assert np.all(np.diff(pos, axis=1) > 0)
+        if G > W:
+            # job W starts only after the whole of job 0: about W jobs in flight
+            assert int(np.sum(pos[0] < pos[W, 0])) == n
+        if G > 1:
+            # job 1 starts once job 0 is a fraction 1 / W through its list
+            assert int(np.sum(pos[0] < pos[1, 0])) == min(n, 1 + n // W)
