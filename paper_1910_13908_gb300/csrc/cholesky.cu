@@ -215,7 +215,7 @@ __device__ __forceinline__ void gemm_nt(float acc[4][4], const float* X, const f
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 2
+#pragma unroll
   for (int m = 0; m < kNB; m += 4) {
     float4 x[4], y[4];
 #pragma unroll
@@ -311,19 +311,20 @@ __device__ __forceinline__ void st16(double* p, const double (&v)[16]) {
 }
 
 // In-place Cholesky of the 64x64 SPD tile in sm (pitch of the tile, lower
-// part read), writing L (upper part zeroed) to sm and L^-1 to sv.
+// part read), writing L (upper part zeroed) to sm and L^-1 to sv
+// (potrf_tile_w below).
 //
 // Gaussian elimination in LDL^T form over the rows of [A | Y], Y = I at the
-// start, four columns per step.  With A = L' D L'^T (L' unit lower,
+// start, W columns per step.  With A = L' D L'^T (L' unit lower,
 // D = diag(p)), L = L' D^1/2 and L^-1 = D^-1/2 L'^-1; the elimination turns
-// Y into L'^-1.  Step k eliminates columns K = k..k+3 at once: with
-// V = A[:, K] and W = Y[K, :] as they stand before the step, and the 4x4
+// Y into L'^-1.  Step k eliminates columns K = k..k+W-1 at once: with
+// V = A[:, K] and Z = Y[K, :] as they stand before the step, and the W x W
 // pivot block V[K, :] = L_D P L_D^T factorised by every thread, row i gets
 //   u_i = V[i, :] L_D^-T          (A[i][k+m] at step k+m: final for column k+m)
 //   g_i[m] = u_i[m] / p_m         (zero unless i > k+m)
 //   c_i = g_i L_D^-1
-//   A[i][j] -= c_i . V[j, :]      (j > k+3)
-//   Y[i][:] -= c_i . W            (equals the four single-column steps)
+//   A[i][j] -= c_i . V[j, :]      (j > k+W-1)
+//   Y[i][:] -= c_i . Z            (equals the W single-column steps)
 // Afterwards L[i][j] = A[i][j] / sqrt(p_j) for j < i, L[j][j] = sqrt(p_j),
 // (L^-1)[i][c] = Y[i][c] / sqrt(p_i).  A non-positive pivot is replaced by
 // 1 and sets *bad.
@@ -332,8 +333,7 @@ __device__ __forceinline__ void st16(double* p, const double (&v)[16]) {
 // of rows 32 (w & 1) .. +31, one row per lane, 16 entries of A and 16 of Y
 // in registers.  Each step reads the published columns K of A and rows K of
 // Y from shared memory (double-buffered, one barrier per step); the owners
-// of the next four columns and rows publish them.  aux holds 1088 scratch
-// values.
+// of the next W columns and rows publish them.
 template <typename R>
 __device__ __forceinline__ R pivot_guard(R p, int* bad) {
   if (!(p > (R)0)) {
@@ -343,14 +343,29 @@ __device__ __forceinline__ R pivot_guard(R p, int* bad) {
   return p;
 }
 
-template <typename R>
-__device__ void potrf_tile(R* sm, R* sv, R* aux, int* bad) {
+// Columns per elimination step of potrf_tile.  8 halves the steps (and
+// barriers) of 4, each a longer chain of pivots; measured at order 4096 on
+// GB300 it was no faster (1237 against 1233 us per factorisation), so 4.
+#ifndef SC_POTRF_W
+#define SC_POTRF_W 4
+#endif
+
+// The elimination above, W columns per step (W = 4 or 8).  The pivot
+// block V[K, :] (W x W) is factorised by every thread in LDL^T form by
+// right-looking elimination; a row's u, g and c follow the formulas above
+// with W terms; the updates add the W rank-one terms in column order.
+// aux: [2][W][64] published columns, [2][W][64] published rows of Y, [64]
+// pivots (4 W 64 + 64 values).
+template <int W, typename R>
+__device__ void potrf_tile_w(R* sm, R* sv, R* aux, int* bad) {
+  static_assert(W == 4 || W == 8, "4 or 8 columns per step");
   constexpr int LD = Pitch<R>::value;
+  constexpr int S = 16 / W;  // steps per 16-column block
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp >> 1, i = 32 * (warp & 1) + lane, cb = 16 * q;
-  R* colb = aux;        // [2][4][64]: colb[m][j] = A[j][k+m]
-  R* rowb = aux + 512;  // [2][4][64]: rowb[m][c] = Y[k+m][c]
-  R* piv = aux + 1024;  // [64] pivots
+  R* colb = aux;               // [2][W][64]: colb[m][j] = A[j][k+m]
+  R* rowb = aux + 2 * W * 64;  // [2][W][64]: rowb[m][c] = Y[k+m][c]
+  R* piv = aux + 4 * W * 64;   // [64] pivots
   R a[16], y[16];
   ld16(sm + i * LD + cb, a);
   Static<0, 16>::each([&](auto tt) {
@@ -358,111 +373,105 @@ __device__ void potrf_tile(R* sm, R* sv, R* aux, int* bad) {
     y[t] = (cb + t == i) ? (R)1 : (R)0;
   });
   if (q == 0) {
-    colb[i] = a[0];
-    colb[64 + i] = a[1];
-    colb[128 + i] = a[2];
-    colb[192 + i] = a[3];
+#pragma unroll
+    for (int m = 0; m < W; ++m) colb[64 * m + i] = a[m];
   }
-  if (i < 4) st16(rowb + 64 * i + cb, y);
+  if (i < W) st16(rowb + 64 * i + cb, y);
   __syncthreads();
   for (int kb = 0; kb < 4; ++kb) {
-    Static<0, 4>::each([&](auto kq_) {
+    Static<0, S>::each([&](auto kq_) {
       constexpr int kq = decltype(kq_)::value;
-      constexpr int bsel = kq & 1;  // parity of the step index 4 kb + kq
-      constexpr int t0 = 4 * kq;    // first column of K inside block q == kb
+      constexpr int bsel = kq & 1;  // parity of the step index S kb + kq (S = 2 or 4, so S kb is even)
+      constexpr int t0 = W * kq;    // first column of K inside block q == kb
       const int k = 16 * kb + t0;
-      const R* col = colb + 256 * bsel;
-      const R* row = rowb + 256 * bsel;
-      R* coln = colb + 256 * (bsel ^ 1);
-      R* rown = rowb + 256 * (bsel ^ 1);
-      // pivot block (lower part) and this row's entries in columns K
-      const R d00 = col[k], d10 = col[k + 1], d20 = col[k + 2], d30 = col[k + 3];
-      const R d11 = col[64 + k + 1], d21 = col[64 + k + 2], d31 = col[64 + k + 3];
-      const R d22 = col[128 + k + 2], d32 = col[128 + k + 3];
-      const R d33 = col[192 + k + 3];
-      const R x0 = col[i], x1 = col[64 + i], x2 = col[128 + i], x3 = col[192 + i];
-      // pivot block = L_D diag(p) L_D^T
-      const R p0 = pivot_guard(d00, bad), r0 = pivot_rcp(p0);
-      const R l10 = d10 * r0, l20 = d20 * r0, l30 = d30 * r0;
-      const R p1 = pivot_guard(fma(-l10, d10, d11), bad), r1 = pivot_rcp(p1);
-      const R e21 = fma(-l20, d10, d21), e31 = fma(-l30, d10, d31);
-      const R l21 = e21 * r1, l31 = e31 * r1;
-      const R p2 = pivot_guard(fma(-l21, e21, fma(-l20, d20, d22)), bad), r2 = pivot_rcp(p2);
-      const R e32 = fma(-l31, e21, fma(-l30, d20, d32));
-      const R l32 = e32 * r2;
-      const R p3 = pivot_guard(fma(-l32, e32, fma(-l31, e31, fma(-l30, d30, d33))), bad), r3 = pivot_rcp(p3);
+      const R* col = colb + W * 64 * bsel;
+      const R* row = rowb + W * 64 * bsel;
+      R* coln = colb + W * 64 * (bsel ^ 1);
+      R* rown = rowb + W * 64 * (bsel ^ 1);
+      // pivot block E = V[K, :] (lower part), eliminated in place: L, p
+      R E[W][W], L[W][W], p[W], r[W];
+#pragma unroll
+      for (int m = 0; m < W; ++m)
+#pragma unroll
+        for (int n = 0; n <= m; ++n) E[m][n] = col[64 * n + k + m];
+#pragma unroll
+      for (int n = 0; n < W; ++n) {
+        p[n] = pivot_guard(E[n][n], bad);
+        r[n] = pivot_rcp(p[n]);
+#pragma unroll
+        for (int m = n + 1; m < W; ++m) L[m][n] = E[m][n] * r[n];
+#pragma unroll
+        for (int m = n + 1; m < W; ++m)
+#pragma unroll
+          for (int o = n + 1; o <= m; ++o) E[m][o] = fma(-L[m][n], E[o][n], E[m][o]);
+      }
       if (threadIdx.x == 0) {
-        piv[k] = p0;
-        piv[k + 1] = p1;
-        piv[k + 2] = p2;
-        piv[k + 3] = p3;
+#pragma unroll
+        for (int m = 0; m < W; ++m) piv[k + m] = p[m];
       }
       // this row: u = V[i,:] L_D^-T, g = masked u / p, c = g L_D^-1
-      const R u0 = x0;
-      const R u1 = fma(-l10, u0, x1);
-      const R u2 = fma(-l21, u1, fma(-l20, u0, x2));
-      const R u3 = fma(-l32, u2, fma(-l31, u1, fma(-l30, u0, x3)));
-      const R g0 = i > k ? u0 * r0 : (R)0;
-      const R g1 = i > k + 1 ? u1 * r1 : (R)0;
-      const R g2 = i > k + 2 ? u2 * r2 : (R)0;
-      const R g3 = i > k + 3 ? u3 * r3 : (R)0;
-      const R c3 = g3;
-      const R c2 = fma(-c3, l32, g2);
-      const R c1 = fma(-c3, l31, fma(-c2, l21, g1));
-      const R c0 = fma(-c3, l30, fma(-c2, l20, fma(-c1, l10, g0)));
-      // A[i][j] -= c . V[j,:] for the columns j > k+3 of this block
+      R u[W], c[W];
+#pragma unroll
+      for (int m = 0; m < W; ++m) {
+        u[m] = col[64 * m + i];
+#pragma unroll
+        for (int n = 0; n < m; ++n) u[m] = fma(-L[m][n], u[n], u[m]);
+      }
+#pragma unroll
+      for (int m = W - 1; m >= 0; --m) {
+        c[m] = i > k + m ? u[m] * r[m] : (R)0;
+#pragma unroll
+        for (int n = m + 1; n < W; ++n) c[m] = fma(-c[n], L[n][m], c[m]);
+      }
+      // A[i][j] -= c . V[j,:] for the columns j > k+W-1 of this block
       if (q >= kb) {
-        R v0[16], v1[16], v2[16], v3[16];
-        ld16(col + cb, v0);
-        ld16(col + 64 + cb, v1);
-        ld16(col + 128 + cb, v2);
-        ld16(col + 192 + cb, v3);
-        if (q > kb) {
-          Static<0, 16>::each([&](auto tt) {
-            constexpr int t = decltype(tt)::value;
-            a[t] = fma(-c3, v3[t], fma(-c2, v2[t], fma(-c1, v1[t], fma(-c0, v0[t], a[t]))));
-          });
-        } else {
-          a[t0] = u0;
-          a[t0 + 1] = u1;
-          a[t0 + 2] = u2;
-          a[t0 + 3] = u3;
-          Static<t0 + 4, 16>::each([&](auto tt) {
-            constexpr int t = decltype(tt)::value;
-            a[t] = fma(-c3, v3[t], fma(-c2, v2[t], fma(-c1, v1[t], fma(-c0, v0[t], a[t]))));
-          });
+        if (q == kb) {
+#pragma unroll
+          for (int m = 0; m < W; ++m) a[t0 + m] = u[m];
+        }
+#pragma unroll
+        for (int m = 0; m < W; ++m) {
+          R v[16];
+          ld16(col + 64 * m + cb, v);
+          if (q > kb) {
+            Static<0, 16>::each([&](auto tt) {
+              constexpr int t = decltype(tt)::value;
+              a[t] = fma(-c[m], v[t], a[t]);
+            });
+          } else {
+            Static<t0 + W, 16>::each([&](auto tt) {
+              constexpr int t = decltype(tt)::value;
+              a[t] = fma(-c[m], v[t], a[t]);
+            });
+          }
         }
       }
       // Y[i][:] -= c . W; W[m][col] is zero right of column k+m
       if (q <= kb) {
-        R w0[16], w1[16], w2[16], w3[16];
-        ld16(row + cb, w0);
-        ld16(row + 64 + cb, w1);
-        ld16(row + 128 + cb, w2);
-        ld16(row + 192 + cb, w3);
-        Static<0, 16>::each([&](auto tt) {
-          constexpr int t = decltype(tt)::value;
-          y[t] = fma(-c3, w3[t], fma(-c2, w2[t], fma(-c1, w1[t], fma(-c0, w0[t], y[t]))));
-        });
+#pragma unroll
+        for (int m = 0; m < W; ++m) {
+          R w[16];
+          ld16(row + 64 * m + cb, w);
+          Static<0, 16>::each([&](auto tt) {
+            constexpr int t = decltype(tt)::value;
+            y[t] = fma(-c[m], w[t], y[t]);
+          });
+        }
       }
-      // publish the next four columns of A and rows of Y
-      if (k + 4 < 64) {
-        if constexpr (kq < 3) {
+      // publish the next W columns of A and rows of Y
+      if (k + W < 64) {
+        if constexpr (kq < S - 1) {
           if (q == kb) {
-            coln[i] = a[t0 + 4];
-            coln[64 + i] = a[t0 + 5];
-            coln[128 + i] = a[t0 + 6];
-            coln[192 + i] = a[t0 + 7];
+#pragma unroll
+            for (int m = 0; m < W; ++m) coln[64 * m + i] = a[t0 + W + m];
           }
         } else {
           if (q == kb + 1) {
-            coln[i] = a[0];
-            coln[64 + i] = a[1];
-            coln[128 + i] = a[2];
-            coln[192 + i] = a[3];
+#pragma unroll
+            for (int m = 0; m < W; ++m) coln[64 * m + i] = a[m];
           }
         }
-        if (i >= k + 4 && i < k + 8) st16(rown + 64 * (i - k - 4) + cb, y);
+        if (i >= k + W && i < k + 2 * W) st16(rown + 64 * (i - k - W) + cb, y);
       }
       __syncthreads();
     });
@@ -480,6 +489,11 @@ __device__ void potrf_tile(R* sm, R* sv, R* aux, int* bad) {
   st16(sm + i * LD + cb, a);
   st16(sv + i * LD + cb, y);
   __syncthreads();
+}
+
+template <typename R>
+__device__ __forceinline__ void potrf_tile(R* sm, R* sv, R* aux, int* bad) {
+  potrf_tile_w<SC_POTRF_W>(sm, sv, aux, bad);
 }
 
 // ---- tensor-core tile products (tcgen05, 3xTF32) ---------------------------------------
@@ -730,6 +744,22 @@ __device__ __forceinline__ void task_operands_async(int4 tk, const R* A, int lda
   async_commit();
 }
 
+// Queues the operand tiles of a TRSM (A_ij, Linv_jj) into X and Y, or of an
+// UPDATE (L_ij, L_kj) into X and Y with its output tile A_ik into O, as one
+// cp.async group: the block then holds no copy of the output in registers.
+template <typename R>
+__device__ __forceinline__ void task_tiles_async(int4 tk, const R* A, int lda, const R* Linv, R* X, R* Y, R* O) {
+  const int i = tk.y, k = tk.z, j = tk.w;
+  copy_tile_async(X, A + (size_t)i * kNB * lda + (size_t)j * kNB, lda);
+  if (tk.x == T_TRSM) {
+    copy_tile_async(Y, Linv + (size_t)j * kNB * kNB, kNB);
+  } else {
+    copy_tile_async(Y, A + (size_t)k * kNB * lda + (size_t)j * kNB, lda);
+    copy_tile_async(O, A + (size_t)i * kNB * lda + (size_t)k * kNB, lda);
+  }
+  async_commit();
+}
+
 // Persistent tile-DAG factorisation.  The block that claims task 0 becomes
 // the walker.  Every other block runs TRSM and UPDATE tasks in
 // list order, two deep: while it multiplies the current task, the operands
@@ -753,6 +783,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
   auto Xb = [&](int b) { return b ? s2 : s0; };  // buffer pairs (s0, s1) and (s2, aux)
   auto Yb = [&](int b) { return b ? aux : s1; };
   __shared__ int s_task, s_ok, s_bad;
+  __shared__ int4 s_tk;  // the task at s_task, decoded once by thread 0
   SyncView sv(sync, nT);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   int next = -1;  // thread 0: the claimed, not yet examined task
@@ -778,6 +809,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
       if (threadIdx.x == 0) {
         s_task = next >= 0 ? next : claim();
         next = -1;
+        s_tk = chol_task(nT, s_task);
       }
       __syncthreads();
       const int t = s_task;
@@ -787,7 +819,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
         chol_walker(A, lda, nT, Linv, sv, status, lm, s0, s1, s2, aux, &s_bad, &s_ok);
         break;
       }
-      cur = chol_task(nT, t);
+      cur = s_tk;
       if (walker_task(cur)) continue;
       if (threadIdx.x == 0) next = claim();
       bool ok = true;
@@ -805,13 +837,16 @@ __global__ void __launch_bounds__(kCholThreads) k_chol(R* __restrict__ A, int ld
       have = true;
     }
     // look at the claimed next task; queue its operands if it is ready
-    if (threadIdx.x == 0) s_task = next;
+    if (threadIdx.x == 0) {
+      s_task = next;
+      if (next >= 0) s_tk = chol_task(nT, next);
+    }
     __syncthreads();
     const int t2 = s_task;
     int4 nxt = make_int4(-1, 0, 0, 0);
     bool staged = false;
     if (t2 >= 0 && t2 < n_tasks) {
-      nxt = chol_task(nT, t2);
+      nxt = s_tk;
       if (walker_task(nxt)) {
         if (threadIdx.x == 0) next = -1;  // done by the walker: skip it
       } else {
@@ -898,6 +933,41 @@ __device__ __forceinline__ void batch_task(const uint32_t* __restrict__ order, i
 // k_chol (its walker's POTRF, TRSM and diagonal UPDATE included), so every
 // job's factor is bit for bit the one k_chol gives.  The counter is job 0's;
 // tiles, counters, status and LM state are the task's job's.
+// POTRF(j) of one job of a batch, by the whole block: waits for the tile's
+// updates, factorises it in shared memory (s0 = L_jj, s1 = Linv_jj, aux
+// scratch) and publishes it.  Out of line, so that its registers do not
+// weigh on the tile products of the batch kernel's main loop.  False if the
+// wait gave up.
+template <typename R>
+__device__ __noinline__ bool batch_potrf(R* A, int lda, int nT, R* Linv, int j, const SyncView& sv,
+                                         uint32_t* status, LMState* lm, R* s0, R* s1, R* aux, int* s_ok,
+                                         int* s_bad) {
+  if (threadIdx.x == 0) {
+    *s_ok = wait_ge(sv.upd + j * nT + j, j, status);
+    *s_bad = 0;
+  }
+  __syncthreads();
+  if (!*s_ok) {
+    if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
+    return false;
+  }
+  R* Ajj = A + (size_t)j * kNB * lda + (size_t)j * kNB;
+  load_tile(s0, Ajj, lda);
+  __syncthreads();
+  potrf_tile(s0, s1, aux, s_bad);
+  store_tile(Ajj, lda, s0);
+  store_tile(Linv + (size_t)j * kNB * kNB, kNB, s1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (*s_bad) {
+      atomicOr(status, SC_STATUS_NOTPD);
+      if (lm != nullptr) lm->notpd = 1;
+    }
+    st_release(sv.pdone + j, 1);
+  }
+  return true;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_batch(R* __restrict__ A0, int lda, int nT,
                                                             R* __restrict__ Linv0, int n_tasks, int G, size_t js,
@@ -909,9 +979,13 @@ __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_b
   R* s1 = s0 + kNB * LD;
   R* s2 = s1 + kNB * LD;
   R* aux = s2 + kNB * LD;  // POTRF scratch; the second Y buffer otherwise
+  R* o0 = aux + kNB * LD;   // an UPDATE's output tile, per buffer pair
+  R* o1 = o0 + kNB * LD;
   auto Xb = [&](int b) { return b ? s2 : s0; };
   auto Yb = [&](int b) { return b ? aux : s1; };
-  __shared__ int s_task, s_ok, s_bad;
+  auto Ob = [&](int b) { return b ? o1 : o0; };
+  __shared__ int s_task, s_ok, s_bad, s_job;
+  __shared__ int4 s_tk;  // the task at s_task and its job, decoded once by thread 0
   int* const counter = SyncView(sync0, nT).fctr;
   const int total = n_tasks * G;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -926,12 +1000,17 @@ __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_b
       if (threadIdx.x == 0) {
         s_task = next >= 0 ? next : atomicAdd(counter, 1);
         next = -1;
+        if (s_task < total) {
+          int jb, tt;
+          batch_task(order, s_task, G, n_tasks, jb, tt);
+          s_job = jb;
+          if (jb >= 0) s_tk = chol_task(nT, tt);
+        }
       }
       __syncthreads();
       const int m = s_task;
       if (m >= total) break;
-      int job, t;
-      batch_task(order, m, G, n_tasks, job, t);
+      const int job = s_job;
       if (job < 0) continue;
       LMState* lm = job_ptr(lm0, js, job);
       if (lm != nullptr && lm->done) continue;
@@ -939,33 +1018,10 @@ __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_b
       R* Linv = job_ptr(Linv0, js, job);
       const SyncView sv(job_ptr(sync0, js, job), nT);
       uint32_t* status = job_ptr(status0, js, job);
-      cur = chol_task(nT, t);
+      cur = s_tk;
       cjob = job;
       if (cur.x == T_POTRF) {
-        const int j = cur.w;
-        if (threadIdx.x == 0) {
-          s_ok = wait_ge(sv.upd + j * nT + j, j, status);
-          s_bad = 0;
-        }
-        __syncthreads();
-        if (!s_ok) {
-          if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
-          break;
-        }
-        R* Ajj = A + (size_t)j * kNB * lda + (size_t)j * kNB;
-        load_tile(s0, Ajj, lda);
-        __syncthreads();
-        potrf_tile(s0, s1, aux, &s_bad);  // s0 = L_jj, s1 = Linv_jj
-        store_tile(Ajj, lda, s0);
-        store_tile(Linv + (size_t)j * kNB * kNB, kNB, s1);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          if (s_bad) {
-            atomicOr(status, SC_STATUS_NOTPD);
-            if (lm != nullptr) lm->notpd = 1;
-          }
-          st_release(sv.pdone + j, 1);
-        }
+        if (!batch_potrf(A, lda, nT, Linv, cur.w, sv, status, lm, s0, s1, aux, &s_ok, &s_bad)) break;
         continue;
       }
       if (threadIdx.x == 0) next = atomicAdd(counter, 1);
@@ -980,25 +1036,32 @@ __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_b
         if (threadIdx.x == 0 && lm != nullptr) lm->notpd = 1;
         break;
       }
-      task_operands_async(cur, A, lda, Linv, Xb(buf), Yb(buf));
+      task_tiles_async(cur, A, lda, Linv, Xb(buf), Yb(buf), Ob(buf));
       have = true;
     }
     // look at the claimed next task; queue its operands if it is a ready
     // TRSM or UPDATE (a POTRF waits for the buffers to be free)
-    if (threadIdx.x == 0) s_task = next;
+    if (threadIdx.x == 0) {
+      s_task = next;
+      if (next >= 0 && next < total) {
+        int jb, tt;
+        batch_task(order, next, G, n_tasks, jb, tt);
+        s_job = jb;
+        if (jb >= 0) s_tk = chol_task(nT, tt);
+      }
+    }
     __syncthreads();
     const int t2 = s_task;
     int4 nxt = make_int4(-1, 0, 0, 0);
     int njob = 0;
     bool staged = false;
     if (t2 >= 0 && t2 < total) {
-      int nt;
-      batch_task(order, t2, G, n_tasks, njob, nt);
+      njob = s_job;
       const LMState* nlm = njob < 0 ? nullptr : job_ptr(lm0, js, njob);
       if (njob < 0 || (nlm != nullptr && nlm->done)) {
         if (threadIdx.x == 0) next = -1;  // a finished job: nothing to do
       } else {
-        nxt = chol_task(nT, nt);
+        nxt = s_tk;
         if (nxt.x != T_POTRF) {
           const SyncView nsv(job_ptr(sync0, js, njob), nT);
           bool ready = true;
@@ -1011,8 +1074,8 @@ __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_b
           staged = __syncthreads_and(ready) != 0;
           if (staged) {
             if (threadIdx.x == 0) next = atomicAdd(counter, 1);
-            task_operands_async(nxt, job_ptr(A0, js, njob), lda, job_ptr(Linv0, js, njob), Xb(buf ^ 1),
-                                Yb(buf ^ 1));
+            task_tiles_async(nxt, job_ptr(A0, js, njob), lda, job_ptr(Linv0, js, njob), Xb(buf ^ 1), Yb(buf ^ 1),
+                             Ob(buf ^ 1));
           }
         }
       }
@@ -1023,13 +1086,6 @@ __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_b
     const int i = cur.y, k = cur.z, j = cur.w;
     const bool trsm = cur.x == T_TRSM;
     R* Out = A + (size_t)i * kNB * lda + (size_t)(trsm ? j : k) * kNB;
-    R old[4][4];  // an UPDATE's output tile, fetched while the operands arrive
-    if (!trsm) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) old[a][b] = __ldcg(Out + (size_t)(ty + 16 * a) * lda + tx + 16 * b);
-    }
     if (staged) async_wait_prev();
     else async_wait_all();
     __syncthreads();
@@ -1039,7 +1095,8 @@ __global__ void __launch_bounds__(kCholThreads, sizeof(R) == 4 ? 2 : 1) k_chol_b
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b)
-        __stcg(Out + (size_t)(ty + 16 * a) * lda + tx + 16 * b, trsm ? acc[a][b] : old[a][b] - acc[a][b]);
+        __stcg(Out + (size_t)(ty + 16 * a) * lda + tx + 16 * b,
+               trsm ? acc[a][b] : Ob(buf)[(ty + 16 * a) * LD + tx + 16 * b] - acc[a][b]);
     __syncthreads();  // the tile is stored and buffer pair buf is free
     if (threadIdx.x == 32) {
       if (trsm) st_release(sv.tdone + i * nT + j, 1);
@@ -1087,6 +1144,7 @@ __global__ void __launch_bounds__(kCholThreads, 2) k_chol_tc(const __grid_consta
   uint64_t* bar_mma = bar_load + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_load + 3);
   int* ctl = reinterpret_cast<int*>(bar_load + 4);  // s_task, s_ok, s_bad
+  __shared__ int4 s_tk;  // the task at ctl[0], decoded once by thread 0
   // the walker's tiles reuse the operand region (padded layout, 3.5 tiles)
   constexpr int LD = Pitch<float>::value;
   float* T0 = reinterpret_cast<float*>(base);
@@ -1151,6 +1209,7 @@ __global__ void __launch_bounds__(kCholThreads, 2) k_chol_tc(const __grid_consta
       if (threadIdx.x == 0) {
         ctl[0] = next >= 0 ? next : claim();
         next = -1;
+        s_tk = chol_task(nT, ctl[0]);
       }
       __syncthreads();
       const int t = ctl[0];
@@ -1160,7 +1219,7 @@ __global__ void __launch_bounds__(kCholThreads, 2) k_chol_tc(const __grid_consta
         chol_walker(A, lda, nT, Linv, sv, status, lm, T0, T1, T2, aux, ctl + 2, ctl + 1);
         break;
       }
-      cur = chol_task(nT, t);
+      cur = s_tk;
       if (walker_task(cur)) continue;
       if (threadIdx.x == 0) next = claim();
       bool ok = true;
@@ -1179,13 +1238,16 @@ __global__ void __launch_bounds__(kCholThreads, 2) k_chol_tc(const __grid_consta
       have = true;
     }
     // look at the claimed next task; queue its operands if it is ready
-    if (threadIdx.x == 0) ctl[0] = next;
+    if (threadIdx.x == 0) {
+      ctl[0] = next;
+      if (next >= 0) s_tk = chol_task(nT, next);
+    }
     __syncthreads();
     const int t2 = ctl[0];
     int4 nxt = make_int4(-1, 0, 0, 0);
     bool staged = false;
     if (t2 >= 0 && t2 < n_tasks) {
-      nxt = chol_task(nT, t2);
+      nxt = s_tk;
       if (walker_task(nxt)) {
         if (threadIdx.x == 0) next = -1;  // done by the walker: skip it
       } else {
@@ -1406,6 +1468,8 @@ static int chol_batch_grid(size_t smem) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const void* fn = reinterpret_cast<const void*>(&k_chol_batch<R>);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // all of the unified L1 as shared memory: two blocks of ~104 KB per SM
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCholThreads, smem);
     return std::max(1, sms * std::min(std::max(per, 1), 4));
   }();
@@ -1418,7 +1482,7 @@ cudaError_t launch_chol_batch(R* A, int lda, int nT, R* Linv, int* sync, uint32_
   const int n_tasks = chol_ntasks(nT);
   if (bt.G < 1 || (long long)n_tasks * bt.G > (1LL << 30)) return cudaErrorInvalidValue;
   if (order != nullptr && (bt.G > 4096 || n_tasks > (1 << 20))) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(R) * (4 * kNB) * Pitch<R>::value;
+  const size_t smem = sizeof(R) * (6 * kNB) * Pitch<R>::value;  // two (X, Y, output) buffer triples
   int grid = std::min<long long>(chol_batch_grid<R>(smem), (long long)n_tasks * bt.G);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   // every job's counters: rows of the reset length at the job stride

@@ -15,6 +15,9 @@
 // real form of dJ_s -> dJ_s H_s with H_s = sum_o w_so J_o^H J_o, and
 // w_so = sum |c_so|^2 (see normal_eqs.cu).
 //
+// The running residual's update in float32 (no statistics) has its own
+// kernel, k_pass_col32, below.
+//
 // Memory: one thread per (baseline, timeslot chunk); consecutive threads take
 // consecutive baselines, whose [F][2][2] complex blocks are contiguous in the
 // [T][B][F][2][2] layout, so every warp streams contiguous memory.
@@ -101,6 +104,94 @@ static cudaError_t go_pass(const Shape& s, const R* Xin, const R* C, const doubl
   return cudaGetLastError();
 }
 
+// ---- the running residual's update in float32 ---------------------------------------------
+//
+// Without statistics, the pass is X + c G_old - c G per visibility
+// (G_old only with P_OLD), G = J_p J_q^H, with the arithmetic of k_pass
+// (the same expressions, so a residual is the same bits with or without
+// its cost, and the mixed path's LM trajectories, which amplify any change
+// of rounding, stay where they were).  What changes is the access: one
+// thread owns one (baseline, channel) column of the [T][B][F][2][2] layout
+// and walks its timeslots, so consecutive threads read consecutive 32-byte
+// visibilities, G_old and G stay in registers, and the loads of several
+// timeslots are issued before their stores (k_pass, one thread per
+// (baseline, timeslot chunk), has one visibility in flight: the compiler
+// cannot move a load above a store that may alias it).
+
+template <int FL>
+__global__ void __launch_bounds__(256) k_pass_col32(int N, int T, int F, int64_t B, const float* Xin,
+                                                    const float* __restrict__ C, const double* __restrict__ J_old,
+                                                    const double* __restrict__ J_cur, float* Rout) {
+  const int64_t cols = B * F;
+  for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < cols;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = col / F;
+    int p, q;
+    bl_pair(b, N, p, q);
+    const m22<float> G = mul_h(load_jones<float>(J_cur, p), load_jones<float>(J_cur, q));
+    m22<float> Go = mzero<float>();
+    if (FL & P_OLD) Go = mul_h(load_jones<float>(J_old, p), load_jones<float>(J_old, q));
+    // may run in place (Rout == Xin): plain loads.  The compiler cannot
+    // move a load above a store that may alias it, so the loads of kTs
+    // timeslots are written before their stores: kTs visibilities in
+    // flight per thread.
+    const float4* x = reinterpret_cast<const float4*>(Xin) + 2 * col;
+    float4* o = reinterpret_cast<float4*>(Rout) + 2 * col;
+    const float2* cp = reinterpret_cast<const float2*>(C) + col;
+    constexpr int kTs = 4;
+    auto update = [&](float4& u, float4& v, float2 cc) {
+      m22<float> xv = {{u.x, u.y}, {u.z, u.w}, {v.x, v.y}, {v.z, v.w}};
+      const cx<float> c = {cc.x, cc.y};
+      if (FL & P_OLD) xv = xv + smul(c, Go);
+      xv = xv - smul(c, G);
+      u = make_float4(xv.a.re, xv.a.im, xv.b.re, xv.b.im);
+      v = make_float4(xv.c.re, xv.c.im, xv.d.re, xv.d.im);
+    };
+    int t = 0;
+    for (; t + kTs <= T; t += kTs) {
+      float4 u[kTs], v[kTs];
+      float2 c[kTs];
+#pragma unroll
+      for (int k = 0; k < kTs; ++k) {
+        const size_t tv = (size_t)(t + k) * cols;
+        u[k] = x[2 * tv];
+        v[k] = x[2 * tv + 1];
+        c[k] = __ldg(cp + tv);
+      }
+#pragma unroll
+      for (int k = 0; k < kTs; ++k) {
+        const size_t tv = (size_t)(t + k) * cols;
+        update(u[k], v[k], c[k]);
+        o[2 * tv] = u[k];
+        o[2 * tv + 1] = v[k];
+      }
+    }
+    for (; t < T; ++t) {
+      const size_t tv = (size_t)t * cols;
+      float4 u = x[2 * tv], v = x[2 * tv + 1];
+      update(u, v, __ldg(cp + tv));
+      o[2 * tv] = u;
+      o[2 * tv + 1] = v;
+    }
+  }
+}
+
+template <int FL>
+static cudaError_t go_pass_col32(const Shape& s, const float* Xin, const float* C, const double* J_old,
+                                 const double* J_cur, float* Rout, cudaStream_t st) {
+  static const int resident = [] {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pass_col32<FL>, 256, 0);
+    return std::max(1, sms * std::max(per, 1));
+  }();
+  const int64_t cols = s.B * s.F;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cols + 255) / 256, resident));
+  k_pass_col32<FL><<<grid, 256, 0, st>>>(s.N, s.T, s.F, s.B, Xin, C, J_old, J_cur, Rout);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, const double* J_old,
                         const double* J_cur, R* Rout, R* stat_cost, R* stat_rho, int nchunk,
@@ -108,6 +199,12 @@ cudaError_t launch_pass(const Shape& s, int flags, const R* Xin, const R* C, con
 #define SC_PASS(FL) \
   case FL:          \
     return go_pass<R, FL>(s, Xin, C, J_old, J_cur, Rout, stat_cost, stat_rho, nchunk, tchunk, lm, st);
+  if constexpr (sizeof(R) == 4) {
+    if (lm == nullptr && flags == (P_SUB | P_WRITE_R))
+      return go_pass_col32<P_SUB | P_WRITE_R>(s, Xin, C, J_old, J_cur, Rout, st);
+    if (lm == nullptr && flags == (P_OLD | P_SUB | P_WRITE_R))
+      return go_pass_col32<P_OLD | P_SUB | P_WRITE_R>(s, Xin, C, J_old, J_cur, Rout, st);
+  }
   switch (flags) {
     SC_PASS(P_SUB | P_STATS)                      // cost (and per-baseline sums) of a residual
     SC_PASS(P_SUB | P_WRITE_R | P_STATS)          // residual + cost

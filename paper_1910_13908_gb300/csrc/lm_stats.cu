@@ -73,24 +73,80 @@ __device__ __forceinline__ void ff_acc_prod(FF& s, float a, float b) {
   s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, p.lo));
 }
 
-// The ten sums of one (chunk, baseline) item from one visibility x and its
-// coherency c.
-__device__ __forceinline__ void stat_add(FF (&a)[kStatV], const m22<float>& x, cx<float> c) {
-  const float xs[8] = {x.a.re, x.a.im, x.b.re, x.b.im, x.c.re, x.c.im, x.d.re, x.d.im};
+// ---- the same on pairs of sums at once -------------------------------------------------------
+//
+// Blackwell's packed float32 instructions (add / sub / mul / fma .rn.f32x2)
+// round each lane exactly as the scalar instruction does, so two
+// accumulators advance in one instruction with the arithmetic above.
+__device__ __forceinline__ unsigned long long pk2(float2 a) { return *reinterpret_cast<unsigned long long*>(&a); }
+__device__ __forceinline__ float2 upk2(unsigned long long d) { return *reinterpret_cast<float2*>(&d); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {  // a b + c, rounded once
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(d);
+}
+struct FF2 {  // two pairs: lane x and lane y
+  float2 hi, lo;
+};
+// s += a b per lane, as ff_acc_prod
+__device__ __forceinline__ void ff2_acc_prod(FF2& s, float2 a, float2 b) {
+  const float2 p = mul2(a, b);
+  const float2 e = fma2(a, b, make_float2(-p.x, -p.y));
+  const float2 t = add2(s.hi, p);
+  const float2 z = sub2(t, s.hi);
+  const float2 tl = add2(sub2(s.hi, sub2(t, z)), sub2(p, z));
+  s.hi = t;
+  s.lo = add2(s.lo, add2(tl, e));
+}
+
+// The ten sums of one (chunk, baseline) item in float32 pairs: rhoX as its
+// (re, im) pairs, two sums per packed instruction, each lane with the
+// operations (and order) of the scalar sum; S and W stay scalar sums in
+// their order (squares of re, im of each entry in turn; c.re^2, c.im^2),
+// so the statistics are the bits the scalar version gives.
+struct Stat32 {
+  FF S, W;
+  FF2 rho[4];
+};
+__device__ __forceinline__ void stat_zero(Stat32& a) {
+  const FF2 z = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  a.S = {0.f, 0.f};
+  a.W = {0.f, 0.f};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) a.rho[e] = z;
+}
+__device__ __forceinline__ void stat_add(Stat32& a, const m22<float>& x, cx<float> c) {
+  const float2 xs[4] = {make_float2(x.a.re, x.a.im), make_float2(x.b.re, x.b.im), make_float2(x.c.re, x.c.im),
+                        make_float2(x.d.re, x.d.im)};
+  const float2 cr = make_float2(c.re, c.re), ci = make_float2(c.im, -c.im);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const float xr = xs[2 * e], xi = xs[2 * e + 1];
-    ff_acc_prod(a[0], xr, xr);
-    ff_acc_prod(a[0], xi, xi);
-    // conj(c) x = (c.re x.re + c.im x.im) + i (c.re x.im - c.im x.re)
-    ff_acc_prod(a[1 + 2 * e], c.re, xr);
-    ff_acc_prod(a[1 + 2 * e], c.im, xi);
-    ff_acc_prod(a[2 + 2 * e], c.re, xi);
-    ff_acc_prod(a[2 + 2 * e], -c.im, xr);
+    ff_acc_prod(a.S, xs[e].x, xs[e].x);
+    ff_acc_prod(a.S, xs[e].y, xs[e].y);
+    // conj(c) x = (c.re x.re + c.im x.im, c.re x.im - c.im x.re)
+    ff2_acc_prod(a.rho[e], cr, xs[e]);
+    ff2_acc_prod(a.rho[e], ci, make_float2(xs[e].y, xs[e].x));
   }
-  ff_acc_prod(a[9], c.re, c.re);
-  ff_acc_prod(a[9], c.im, c.im);
+  ff_acc_prod(a.W, c.re, c.re);
+  ff_acc_prod(a.W, c.im, c.im);
 }
+
+// The ten sums of one (chunk, baseline) item in float64.
 __device__ __forceinline__ void stat_add(double (&a)[kStatV], const m22<double>& x, cx<double> c) {
   const double xs[8] = {x.a.re, x.a.im, x.b.re, x.b.im, x.c.re, x.c.im, x.d.re, x.d.im};
 #pragma unroll
@@ -118,6 +174,17 @@ __device__ __forceinline__ void stat_store(double* stat, int64_t B, int chunk, i
     o[(size_t)(2 * i) * B] = r.hi;
     o[(size_t)(2 * i + 1) * B] = r.lo;
   }
+}
+__device__ __forceinline__ void stat_store(double* stat, int64_t B, int chunk, int64_t b, const Stat32& a) {
+  FF v[kStatV];
+  v[0] = a.S;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    v[1 + 2 * e] = {a.rho[e].hi.x, a.rho[e].lo.x};
+    v[2 + 2 * e] = {a.rho[e].hi.y, a.rho[e].lo.y};
+  }
+  v[9] = a.W;
+  stat_store(stat, B, chunk, b, v);
 }
 
 // ---- the statistics pass ---------------------------------------------------------------------
@@ -253,9 +320,8 @@ __global__ void __launch_bounds__(kStatThreads) k_lm_stats32(int N, int T, int F
     }
   };
   item_begin();
-  FF a[kStatV];
-#pragma unroll
-  for (int i = 0; i < kStatV; ++i) a[i] = {0.f, 0.f};
+  Stat32 a;
+  stat_zero(a);
   while (cs.idx < n_items) {
     issue();
     st_wait<kRing - 1>();  // the consume stage has landed
@@ -269,8 +335,7 @@ __global__ void __launch_bounds__(kStatThreads) k_lm_stats32(int N, int T, int F
     stat_add(a, x, c);
     if (cs.next(F)) {
       stat_store(stat, B, cs.chunk, cs.b, a);
-#pragma unroll
-      for (int i = 0; i < kStatV; ++i) a[i] = {0.f, 0.f};
+      stat_zero(a);
       const int64_t n = cs.idx + stride;
       if (n < n_items) cs.start(n, B, T, tchunk);
       else cs.idx = n_items;
