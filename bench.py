@@ -350,7 +350,13 @@ def measure_predict_full(job, spec, prec, reps, pk):
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/),
 # keyed by (kernel kind, workload); None until captured for the current kernel.
-NCU_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes.sum.per_second x duration) from one ncu
+# capture of the kernel as it stands, by (kernel kind, workload); a kernel
+# changed since its capture has no entry.
+NCU_TRAFFIC = {
+    ("lm_stats", "ska512"): 215e6,      # k_lm_stats32, 5.23 M visibilities
+    ("vis_pass", "ska512"): 321e6,      # k_pass_col32 (P_OLD | P_SUB | P_WRITE_R); part of R is read from L2
+}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -476,6 +482,7 @@ def run_ours(args, rank, world, local_rank):
             r["frac"] = r["achieved"] / r["peak"]
             r["avg_launch_us"] = 1e3 * prof[k][1] / prof[k][0]
             r["launches"] = prof[k][0]
+            r["traffic"] = NCU_TRAFFIC.get((k, args.workload))
             streaming[k] = r
 
     cpu = None
