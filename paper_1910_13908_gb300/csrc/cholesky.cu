@@ -281,6 +281,81 @@ struct Static<N, N> {
   __device__ __forceinline__ static void each(F&&) {}
 };
 
+// gemm_nt restricted to the terms that can be nonzero, for the walker's
+// chain products:
+//   TRI_Y: Y is lower triangular (Y[c][m] = 0 for m > c, as Linv_jj is
+//          stored), so output column block b sums only m < 16 (b + 1);
+//   SYM:   X Y^T is symmetric and only its lower part is read, so only the
+//          16x16 blocks a >= b are formed (the others are left unset).
+// The skipped terms are exact zeros, and the kept ones are added in gemm_nt's
+// order, so every formed entry has gemm_nt's value.
+template <bool TRI_Y, bool SYM>
+__device__ __forceinline__ void gemm_nt_part(float acc[4][4], const float* X, const float* Y) {
+  constexpr int L = Pitch<float>::value;
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  Static<0, 4>::each([&](auto mc_) {  // contraction chunk m = 16 mc .. 16 mc + 15
+    constexpr int mc = decltype(mc_)::value;
+#pragma unroll
+    for (int m = 16 * mc; m < 16 * mc + 16; m += 4) {
+      float4 x[4], y[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) x[a] = *reinterpret_cast<const float4*>(X + (ty + 16 * a) * L + m);
+      Static<0, 4>::each([&](auto b_) {
+        constexpr int b = decltype(b_)::value;
+        if constexpr (!TRI_Y || b >= mc) y[b] = *reinterpret_cast<const float4*>(Y + (tx + 16 * b) * L + m);
+      });
+      Static<0, 4>::each([&](auto a_) {
+        constexpr int a = decltype(a_)::value;
+        Static<0, 4>::each([&](auto b_) {
+          constexpr int b = decltype(b_)::value;
+          if constexpr ((!TRI_Y || b >= mc) && (!SYM || a >= b)) {
+            float t = acc[a][b];
+            t = fmaf(x[a].x, y[b].x, t);
+            t = fmaf(x[a].y, y[b].y, t);
+            t = fmaf(x[a].z, y[b].z, t);
+            t = fmaf(x[a].w, y[b].w, t);
+            acc[a][b] = t;
+          }
+        });
+      });
+    }
+  });
+}
+template <bool TRI_Y, bool SYM>
+__device__ __forceinline__ void gemm_nt_part(double acc[4][4], const double* X, const double* Y) {
+  constexpr int L = Pitch<double>::value;
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  Static<0, 4>::each([&](auto mc_) {
+    constexpr int mc = decltype(mc_)::value;
+#pragma unroll 2
+    for (int m = 16 * mc; m < 16 * mc + 16; m += 2) {
+      double2 x[4], y[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) x[a] = *reinterpret_cast<const double2*>(X + (ty + 16 * a) * L + m);
+      Static<0, 4>::each([&](auto b_) {
+        constexpr int b = decltype(b_)::value;
+        if constexpr (!TRI_Y || b >= mc) y[b] = *reinterpret_cast<const double2*>(Y + (tx + 16 * b) * L + m);
+      });
+      Static<0, 4>::each([&](auto a_) {
+        constexpr int a = decltype(a_)::value;
+        Static<0, 4>::each([&](auto b_) {
+          constexpr int b = decltype(b_)::value;
+          if constexpr ((!TRI_Y || b >= mc) && (!SYM || a >= b))
+            acc[a][b] = fma(x[a].y, y[b].y, fma(x[a].x, y[b].x, acc[a][b]));
+        });
+      });
+    }
+  });
+}
+
 // 16 consecutive values at a 16-byte aligned shared-memory address.
 __device__ __forceinline__ void ld16(const float* p, float (&v)[16]) {
 #pragma unroll
@@ -329,11 +404,14 @@ __device__ __forceinline__ void st16(double* p, const double (&v)[16]) {
 // (L^-1)[i][c] = Y[i][c] / sqrt(p_i).  A non-positive pivot is replaced by
 // 1 and sets *bad.
 //
-// Thread layout: warp w owns column block q = w / 2 (columns 16q..16q+15)
-// of rows 32 (w & 1) .. +31, one row per lane, 16 entries of A and 16 of Y
+// Thread layout: warp w owns column block q = w % 4 (columns 16q..16q+15)
+// of rows 32 (w / 4) .. +31, one row per lane, 16 entries of A and 16 of Y
 // in registers.  Each step reads the published columns K of A and rows K of
 // Y from shared memory (double-buffered, one barrier per step); the owners
-// of the next W columns and rows publish them.
+// of the next W columns and rows publish them.  Once k >= 32 the rows 0..31
+// are final (their multipliers c are zero), so their warps skip the row
+// work and only take part in the pivots and the barriers; warp w runs on
+// scheduler w % 4 of the SM, so each scheduler keeps one working warp.
 template <typename R>
 __device__ __forceinline__ R pivot_guard(R p, int* bad) {
   if (!(p > (R)0)) {
@@ -362,7 +440,7 @@ __device__ void potrf_tile_w(R* sm, R* sv, R* aux, int* bad) {
   constexpr int LD = Pitch<R>::value;
   constexpr int S = 16 / W;  // steps per 16-column block
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q = warp >> 1, i = 32 * (warp & 1) + lane, cb = 16 * q;
+  const int q = warp & 3, h = warp >> 2, i = 32 * h + lane, cb = 16 * q;
   R* colb = aux;               // [2][W][64]: colb[m][j] = A[j][k+m]
   R* rowb = aux + 2 * W * 64;  // [2][W][64]: rowb[m][c] = Y[k+m][c]
   R* piv = aux + 4 * W * 64;   // [64] pivots
@@ -408,6 +486,11 @@ __device__ void potrf_tile_w(R* sm, R* sv, R* aux, int* bad) {
       if (threadIdx.x == 0) {
 #pragma unroll
         for (int m = 0; m < W; ++m) piv[k + m] = p[m];
+      }
+      // every row of this warp is at most k: c = 0, the row work is a no-op
+      if (32 * h + 31 <= k) {
+        __syncthreads();
+        return;
       }
       // this row: u = V[i,:] L_D^-T, g = masked u / p, c = g L_D^-1
       R u[W], c[W];
@@ -652,9 +735,11 @@ __device__ __forceinline__ bool walker_task(int4 tk) {
 // in shared memory and walks the critical path of the factorisation,
 // publishing each result for the other CTAs.  Its own tasks appear in the
 // list in the order it runs them, and it waits only on earlier tasks, so the
-// list-order argument against deadlock still holds.
+// list-order argument against deadlock still holds.  TRSM(j+1, j) skips the
+// zero upper part of Linv_jj, and UPDATE(j+1, j+1, j) forms only the lower
+// blocks that POTRF(j+1) reads; both give the sums of the full products.
 template <typename R>
-__device__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32_t* status, LMState* lm,
+__device__ __noinline__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32_t* status, LMState* lm,
                             R* T0, R* T1, R* T2, R* aux, int* s_bad, int* s_ok) {
   constexpr int LD = Pitch<R>::value;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -686,7 +771,7 @@ __device__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32
     load_tile(T2, Ap, lda);
     __syncthreads();
     R acc[4][4];
-    gemm_nt(acc, T2, T1);
+    gemm_nt_part<true, false>(acc, T2, T1);
     __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -709,11 +794,11 @@ __device__ void chol_walker(R* A, int lda, int nT, R* Linv, SyncView& sv, uint32
     }
     load_tile(T0, A + (size_t)(j + 1) * kNB * lda + (size_t)(j + 1) * kNB, lda);
     __syncthreads();
-    gemm_nt(acc, T2, T2);
+    gemm_nt_part<false, true>(acc, T2, T2);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) T0[(ty + 16 * a) * LD + tx + 16 * b] -= acc[a][b];
+      for (int b = 0; b <= a; ++b) T0[(ty + 16 * a) * LD + tx + 16 * b] -= acc[a][b];
   }
 }
 
