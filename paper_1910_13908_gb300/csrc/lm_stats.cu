@@ -31,6 +31,11 @@ namespace sc {
 
 constexpr int kStatV = 10;  // S, rhoX (8), W
 constexpr int kStatThreads = 256;
+// Blocks of the float32 pass: 128 threads.  At its 72 registers a thread,
+// an SM holds 7 such blocks (28 warps) against 3 of 256 threads (24 warps);
+// each item's sums stay in one thread, so the block size does not change
+// them.
+constexpr int kStat32Threads = 128;
 
 // ---- pairs of floats -------------------------------------------------------------------------
 //
@@ -252,7 +257,7 @@ __device__ __forceinline__ void st_wait() { asm volatile("cp.async.wait_group %0
 }  // namespace
 
 constexpr int kRing = 4;
-constexpr size_t kRingSmem = (size_t)kRing * kStatThreads * (2 * 16 + 8);
+constexpr size_t kRingSmem = (size_t)kRing * kStat32Threads * (2 * 16 + 8);
 
 // Position in one thread's sequence: item idx = (chunk, b), timeslot t of
 // [t0, t1), channel f.
@@ -276,7 +281,7 @@ struct StatCursor {
 };
 
 template <int FL>
-__global__ void __launch_bounds__(kStatThreads) k_lm_stats32(int N, int T, int F, int64_t B, int nchunk, int tchunk,
+__global__ void __launch_bounds__(kStat32Threads) k_lm_stats32(int N, int T, int F, int64_t B, int nchunk, int tchunk,
                                                            const float* __restrict__ Xin,
                                                            const float* __restrict__ C,
                                                            const double* __restrict__ J_old, double* __restrict__ stat,
@@ -284,11 +289,11 @@ __global__ void __launch_bounds__(kStatThreads) k_lm_stats32(int N, int T, int F
   if (nchunk_out != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *nchunk_out = nchunk;
   extern __shared__ __align__(16) unsigned char st_smem[];
   float4* xring = reinterpret_cast<float4*>(st_smem);                                        // [kRing][2][T]
-  float2* cring = reinterpret_cast<float2*>(st_smem + (size_t)kRing * 2 * kStatThreads * 16);  // [kRing][T]
+  float2* cring = reinterpret_cast<float2*>(st_smem + (size_t)kRing * 2 * kStat32Threads * 16);  // [kRing][T]
   const int tid = threadIdx.x;
   const int64_t n_items = (int64_t)nchunk * B;
-  const int64_t stride = (int64_t)gridDim.x * kStatThreads;
-  const int64_t first = (int64_t)blockIdx.x * kStatThreads + tid;
+  const int64_t stride = (int64_t)gridDim.x * kStat32Threads;
+  const int64_t first = (int64_t)blockIdx.x * kStat32Threads + tid;
   StatCursor pf, cs;  // prefetch and consume cursors
   if (first < n_items) pf.start(first, B, T, tchunk);
   else pf.idx = n_items;
@@ -297,9 +302,9 @@ __global__ void __launch_bounds__(kStatThreads) k_lm_stats32(int N, int T, int F
   auto issue = [&]() {
     if (pf.idx < n_items) {
       const size_t v = ((size_t)pf.t * B + pf.b) * F + pf.f;
-      st_cp16(&xring[(pf_stage * 2) * kStatThreads + tid], Xin + 8 * v);
-      st_cp16(&xring[(pf_stage * 2 + 1) * kStatThreads + tid], Xin + 8 * v + 4);
-      st_cp8(&cring[pf_stage * kStatThreads + tid], C + 2 * v);
+      st_cp16(&xring[(pf_stage * 2) * kStat32Threads + tid], Xin + 8 * v);
+      st_cp16(&xring[(pf_stage * 2 + 1) * kStat32Threads + tid], Xin + 8 * v + 4);
+      st_cp8(&cring[pf_stage * kStat32Threads + tid], C + 2 * v);
       if (pf.next(F)) {
         const int64_t n = pf.idx + stride;
         if (n < n_items) pf.start(n, B, T, tchunk);
@@ -325,9 +330,9 @@ __global__ void __launch_bounds__(kStatThreads) k_lm_stats32(int N, int T, int F
   while (cs.idx < n_items) {
     issue();
     st_wait<kRing - 1>();  // the consume stage has landed
-    const float4 u = xring[(cs_stage * 2) * kStatThreads + tid];
-    const float4 w = xring[(cs_stage * 2 + 1) * kStatThreads + tid];
-    const float2 cc = cring[cs_stage * kStatThreads + tid];
+    const float4 u = xring[(cs_stage * 2) * kStat32Threads + tid];
+    const float4 w = xring[(cs_stage * 2 + 1) * kStat32Threads + tid];
+    const float2 cc = cring[cs_stage * kStat32Threads + tid];
     cs_stage = cs_stage + 1 == kRing ? 0 : cs_stage + 1;
     m22<float> x = {{u.x, u.y}, {u.z, u.w}, {w.x, w.y}, {w.z, w.w}};
     const cx<float> c = {cc.x, cc.y};
@@ -373,12 +378,14 @@ struct StatsKernel<float> {
   template <int FL>
   static const void* fn() { return reinterpret_cast<const void*>(&k_lm_stats32<FL>); }
   static constexpr size_t smem = kRingSmem;
+  static constexpr int threads = kStat32Threads;
 };
 template <>
 struct StatsKernel<double> {
   template <int FL>
   static const void* fn() { return reinterpret_cast<const void*>(&k_lm_stats64<FL>); }
   static constexpr size_t smem = 0;
+  static constexpr int threads = kStatThreads;
 };
 
 template <typename R, int FL>
@@ -392,16 +399,16 @@ static cudaError_t go_stats(const Shape& s, const R* Xin, const R* C, const doub
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const void* f = K::template fn<FL>();
     if (K::smem > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, kStatThreads, K::smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, K::threads, K::smem);
     return std::max(1, std::min(sms, kMaxSMs) * std::max(per, 1));
   }();
   int nc = 0, tc = 0;
-  stats_chunks(s.T, s.B, (int64_t)resident * kStatThreads, &nc, &tc);
+  stats_chunks(s.T, s.B, (int64_t)resident * K::threads, &nc, &tc);
   *nchunk = nc;
   const int64_t items = (int64_t)nc * s.B;
-  const unsigned grid = (unsigned)std::min<int64_t>((items + kStatThreads - 1) / kStatThreads, resident);
+  const unsigned grid = (unsigned)std::min<int64_t>((items + K::threads - 1) / K::threads, resident);
   if constexpr (sizeof(R) == 4)
-    k_lm_stats32<FL><<<grid, kStatThreads, K::smem, st>>>(s.N, s.T, s.F, s.B, nc, tc, Xin, C, J_old, stat,
+    k_lm_stats32<FL><<<grid, K::threads, K::smem, st>>>(s.N, s.T, s.F, s.B, nc, tc, Xin, C, J_old, stat,
                                                           nchunk_dev);
   else
     k_lm_stats64<FL><<<grid, kStatThreads, 0, st>>>(s.N, s.T, s.F, s.B, nc, tc, Xin, C, J_old, stat, nchunk_dev);
