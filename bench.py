@@ -348,13 +348,11 @@ def measure_predict_full(job, spec, prec, reps, pk):
             "device_status": status}
 
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/),
-# keyed by (kernel kind, workload); None until captured for the current kernel.
-# DRAM bytes per launch (dram__bytes.sum.per_second x duration) from one ncu
-# capture of the kernel as it stands, by (kernel kind, workload); a kernel
-# changed since its capture has no entry.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the float32 kernel as it stands (profiles/), by (kernel kind,
+# workload); a kernel changed since its capture has no entry.
 NCU_TRAFFIC = {
-    ("lm_stats", "ska512"): 215e6,      # k_lm_stats32, 5.23 M visibilities
+    ("cholesky", "ska512"): 38.4e6,     # k_chol<float>, order 4096; the factor stays in L2 between reads
     ("vis_pass", "ska512"): 321e6,      # k_pass_col32 (P_OLD | P_SUB | P_WRITE_R); part of R is read from L2
 }
 
@@ -471,7 +469,7 @@ def run_ours(args, rank, world, local_rank):
     roof["launches"] = n_dom
     roof["avg_launch_us"] = 1e3 * ms_dom / max(n_dom, 1)
     roof["share_of_step"] = ms_dom / ms if ms > 0 else None
-    roof["traffic"] = NCU_TRAFFIC.get((dominant, args.workload))
+    roof["traffic"] = NCU_TRAFFIC.get((dominant, args.workload)) if args.prec == "mixed" else None
     roof["peak_kind"] = src
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}
     # the streaming kernels' own rooflines (HBM-bound)
@@ -482,7 +480,7 @@ def run_ours(args, rank, world, local_rank):
             r["frac"] = r["achieved"] / r["peak"]
             r["avg_launch_us"] = 1e3 * prof[k][1] / prof[k][0]
             r["launches"] = prof[k][0]
-            r["traffic"] = NCU_TRAFFIC.get((k, args.workload))
+            r["traffic"] = NCU_TRAFFIC.get((k, args.workload)) if args.prec == "mixed" else None
             streaming[k] = r
 
     cpu = None
